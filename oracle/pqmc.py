@@ -99,7 +99,7 @@ class Model:
         self.gap = {}
         for sigma in (+1, -1):
             self.P[sigma], self.gap[sigma] = trial.trial_orbitals(
-                p.kind, self.K, self.eps, p.M_N, self.n_sigma[sigma], sigma, p.tiebreak)
+                p.kind, self.K, self.eps, p.M_N, self.n_sigma[sigma], sigma, p.tiebreak, p.Lx)
         self.alpha = hs.alpha(p.dtau, p.U)
         self.lam = hs.lam(p.g)
 

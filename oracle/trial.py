@@ -16,8 +16,12 @@ degenerate shell.  The trial needs a unique ground state, so:
 * honeycomb: the Neel field is raised to max(M_N, tiebreak), default 1e-4
   (Neel direction: particle-hole symmetry, hence the sign, is kept);
 * square: a spin-independent on-site term tiebreak * w_i is added to the
-  trial Hamiltonian only, w_i = frac(i * 0.6180339887498949) - 0.5,
-  default tiebreak 0.01.
+  trial Hamiltonian only, w_i = cos(pi x_i / 4) + cos(pi y_i / 2) / 2 at site
+  (x_i, y_i), default tiebreak 0.2.  Plane-wave shell states mix only through
+  the Fourier components of the on-site term at their momentum differences;
+  this modulation has them, and opens a gap of 0.03 on the 8x8 t' = -0.2
+  lattice at 28 particles, while a quasi-random term splits that shell by
+  only ~1e-4 and leaves the trial defined to no better than ~1e-12.
 
 G depends only on the span of P_sigma, so any orthonormal basis of it serves.
 """
@@ -25,23 +29,26 @@ import numpy as np
 
 from . import lattice
 
-GOLDEN = 0.6180339887498949
 
 
-def trial_hamiltonian(kind, K, eps, M_N, sigma, tiebreak=-1.0):
+def trial_hamiltonian(kind, K, eps, M_N, sigma, tiebreak=-1.0, lx=None):
     N = K.shape[0]
     if kind == lattice.HONEYCOMB:
         tb = 1e-4 if tiebreak < 0 else tiebreak
         m = max(M_N, tb)
         return K + sigma * m * np.diag(eps)
-    tb = 0.01 if tiebreak < 0 else tiebreak
-    w = np.array([(i * GOLDEN) % 1.0 - 0.5 for i in range(N)])
+    tb = 0.2 if tiebreak < 0 else tiebreak
+    Lx = int(round(lx)) if lx else N
+    x = np.arange(N) % Lx
+    y = np.arange(N) // Lx
+    w = np.cos(np.pi * x / 4.0) + 0.5 * np.cos(np.pi * y / 2.0)
     return K + sigma * M_N * np.diag(eps) + tb * np.diag(w)
 
 
-def trial_orbitals(kind, K, eps, M_N, n_sigma, sigma, tiebreak=-1.0):
-    """P_sigma (N x n_sigma) and the gap above the last occupied level."""
-    h = trial_hamiltonian(kind, K, eps, M_N, sigma, tiebreak)
+def trial_orbitals(kind, K, eps, M_N, n_sigma, sigma, tiebreak=-1.0, lx=None):
+    """P_sigma (N x n_sigma) and the gap above the last occupied level.
+    lx is the extent Lx of a square lattice (site i sits at x = i mod Lx)."""
+    h = trial_hamiltonian(kind, K, eps, M_N, sigma, tiebreak, lx)
     e, v = np.linalg.eigh(h)
     gap = e[n_sigma] - e[n_sigma - 1] if n_sigma < len(e) else np.inf
     return v[:, :n_sigma].copy(), float(gap)

@@ -129,11 +129,16 @@ def test_neel_trial_is_antiferromagnetic(L, M):
 
 
 def test_doped_square_trial_closed_shell():
+    """28 particles on the 8x8 t' = -0.2 lattice fill 27 states below an 8-fold
+    shell at e = -0.4 (Bloch spectrum); the tie-break must open a real gap."""
     K, eps = lattice.square(8, 8, 1.0, -0.2)
-    P, gap = trial.trial_orbitals(lattice.SQUARE, K, eps, 0.0, 28, 1)
-    assert gap > 1e-6
+    e = np.sort(np.linalg.eigvalsh(K))
+    assert np.allclose(e[27:35], -0.4, atol=1e-12) and e[26] < -0.4 - 0.1 and e[35] > -0.4 + 0.1
+    for M, least in ((0.0, 1e-2), (0.1, 1e-3)):
+        P, gap = trial.trial_orbitals(lattice.SQUARE, K, eps, M, 28, 1, lx=8)
+        assert gap > least
     # without the tie-break the shell is open
-    _, gap0 = trial.trial_orbitals(lattice.SQUARE, K, eps, 0.0, 28, 1, tiebreak=0.0)
+    _, gap0 = trial.trial_orbitals(lattice.SQUARE, K, eps, 0.0, 28, 1, tiebreak=0.0, lx=8)
     assert gap0 < 1e-10
 
 
