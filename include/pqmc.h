@@ -1,0 +1,225 @@
+/*
+ * pqmc.h -- C-ABI of libpqmc.so: the projective determinant-QMC sweep with a
+ * Gutzwiller-projected Neel trial state, on one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: W.-X. Chang and Z.-X. Li, "Boosting quantum Monte Carlo and
+ * alleviating sign problem by Gutzwiller projection" (arXiv 2303.13403).
+ *
+ *  - Model: the honeycomb Hubbard model of Eq. (2); also a square t-t' lattice.
+ *  - Trial state: |psi_T> = exp(-g sum_i n_i,up n_i,dn) |psi_N> of Eq. (3), with
+ *    |psi_N> the ground state of the Neel mean-field Hamiltonian H_N
+ *    (honeycomb Hubbard section).
+ *  - Estimator: <psi_T| e^{-Theta H} O e^{-Theta H} |psi_T> / <psi_T| e^{-2 Theta H} |psi_T>
+ *    (Method section), evaluated by determinant QMC.
+ *  - The Gutzwiller factor is decoupled with the Ising field of Eq. (1), read
+ *    in the spin channel (cosh lambda = e^{g/2}); the U term uses the same
+ *    identity with g -> dtau U (cosh alpha = e^{dtau U / 2}).
+ *
+ * Conventions used by every entry point:
+ *  - Slices tau = 0 .. Ltau+1, Ltau = round(two_theta / dtau). Slices 0 and
+ *    Ltau+1 carry the Gutzwiller fields; 1..Ltau the Hubbard fields.
+ *    B_tau = e^{-dtau K} e^{V(s_tau)} (interaction slices),
+ *    B_tau = e^{V(s_tau)} (Gutzwiller slices).
+ *  - Fields are int8 in {-1,+1}, laid out [tau][i], (Ltau+2) x N per chain.
+ *  - Green's functions are G_ij = <c_i c_j^+>, row-major N x N, spin 0 = up,
+ *    spin 1 = down.
+ *  - One sweep is one directional pass that proposes every field once;
+ *    sweeps alternate up (even sweep index) and down (odd). Measurements are
+ *    taken once per sweep at tau = Ltau/2 on the freshly stabilised G.
+ *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11):
+ *    key = (seed low, seed high word), counter = (site, slice, sweep, chain);
+ *    Metropolis uniform u = ((x0 << 21) | (x1 >> 11)) * 2^-53, accept iff
+ *    u < |R|; initial field s = +1 iff bit 0 of x2 is set (sweep = 0xffffffff).
+ *
+ * Memory and ownership: the library allocates and owns all device memory and,
+ * unless a stream is supplied, its own CUDA stream on the device that is
+ * current when the context is created. All pointers in these signatures are
+ * HOST pointers owned by the caller; the library copies from or into them and
+ * keeps no reference after the call returns.
+ *
+ * Errors: every entry point returns a pqmc_status; nothing is thrown across
+ * the ABI and the library never aborts. After PQMC_ESTAB, PQMC_ENAN or
+ * PQMC_ETIMEOUT the context keeps the error (sticky) and refuses further
+ * sweeps; pqmc_last_error() gives a one-line reason. Entry points that read
+ * results synchronise the context's stream first.
+ */
+#ifndef PQMC_H
+#define PQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PQMC_OK = 0,
+    PQMC_EINVAL = 1,    /* bad argument; nothing was changed */
+    PQMC_ENOMEM = 2,    /* device or host allocation failed */
+    PQMC_ECUDA = 3,     /* a CUDA call failed (launch, copy, no device) */
+    PQMC_ESTAB = 4,     /* singular matrix in the stabilisation (zero pivot / zero column) */
+    PQMC_ENAN = 5,      /* NaN or Inf in a ratio or in G */
+    PQMC_ETIMEOUT = 6   /* a bounded device-side wait gave up */
+} pqmc_status;
+
+/* Arithmetic of the wrap and delayed-update products. The stabilisation
+ * (QR, the N_sigma x N_sigma inverse of B_L B_R, log-determinant and sign)
+ * is FP64 in every mode. */
+typedef enum {
+    PQMC_FP64 = 0,      /* everything FP64 */
+    PQMC_FP32 = 1,      /* G, ratios, wrap and updates in FP32 */
+    PQMC_BF16X3 = 2     /* G and ratios FP32; wrap and update products as
+                           three BF16 tensor-core products (hi*hi + hi*lo + lo*hi),
+                           FP32 accumulation */
+} pqmc_precision;
+
+typedef enum { PQMC_HONEYCOMB = 0, PQMC_SQUARE = 1 } pqmc_lattice_kind;
+
+/* Lattice: honeycomb Lx x Ly unit cells (N = 2 Lx Ly; site 2(x + Lx y) + sub,
+ * A(x,y) bonds to B(x,y), B(x-1,y), B(x,y-1)) or square Lx x Ly (N = Lx Ly,
+ * site x + Lx y, hopping -t to nearest and -tp to next-nearest neighbours).
+ * Periodic in both directions; a bond that wraps onto an existing one adds
+ * its amplitude again. */
+typedef struct {
+    int kind;           /* pqmc_lattice_kind */
+    int Lx, Ly;
+    double t, tp;
+} pqmc_lattice;
+
+/* Trial state of Eq. (3): Gutzwiller parameter g >= 0 and the Neel field M_N
+ * of H_N = H_0 + M_N sum_i eps_i (n_up - n_dn), eps_i = +1 on A, -1 on B
+ * (on the square lattice (-1)^(x+y)). N_up/N_dn < 0 mean half filling.
+ * tiebreak < 0 selects the default open-shell tie-break: honeycomb uses the
+ * Neel field max(M_N, 1e-4); square adds tiebreak * (cos(pi x/4) + cos(pi y/2)/2)
+ * on site (x, y), default tiebreak 0.2, to the trial Hamiltonian only. */
+typedef struct {
+    double g, M_N;
+    int N_up, N_dn;
+    double tiebreak;
+} pqmc_trial;
+
+/* One chain of a batch: its own lattice, couplings, projection and trial. */
+typedef struct {
+    pqmc_lattice lattice;
+    double U, dtau, two_theta;
+    pqmc_trial trial;
+} pqmc_chain_spec;
+
+typedef struct {
+    int n_stab;             /* slices between QR stabilisations; Ltau/2 must be a multiple */
+    int delay_k;            /* sites per delayed-update block: 32 (0 selects 32) */
+    int prec;               /* pqmc_precision */
+    uint64_t seed;          /* Philox key */
+    int n_chains;           /* pqmc_init only: identical chains to run (>= 1) */
+    int chain_offset;       /* chain index of the first chain (Philox counter word) */
+    int accept_log;         /* >0: keep the accept/reject bit of the first
+                               accept_log proposals per chain (test hook) */
+    int max_meas;           /* capacity of per-sweep measurement records per chain (0 = 4096) */
+    void* stream;           /* cudaStream_t to run on, or NULL for a library-owned stream */
+} pqmc_opts;
+
+/* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
+ * consecutive sweeps (errors are NaN with fewer than two bins). E is the
+ * energy per site of Eq. (2); docc the double occupancy per site. */
+typedef struct {
+    double E, E_err;
+    double docc, docc_err;
+    double sign, sign_err;
+    double accept;          /* accepted / proposed flips */
+    double max_dG;          /* max |G - G_fresh| over all stabilisations so far */
+    long n_meas;            /* measurements used */
+} pqmc_obs;
+
+typedef struct pqmc_ctx pqmc_ctx;
+
+/* Create a context running opts->n_chains identical chains of one model.
+ * Builds K, e^{-+dtau K}, the trial orbitals P_sigma (host FP64), draws the
+ * initial fields with Philox, uploads everything and computes the left stack
+ * and G at tau = -1 on the device. Returns PQMC_EINVAL if N_sigma > N,
+ * Ltau is odd, Ltau/2 is not a multiple of n_stab, or the trial shell is open
+ * (gap below 1e-8). *out is NULL on failure. */
+pqmc_status pqmc_init(const pqmc_lattice* lattice, double U, double dtau, double two_theta,
+                      const pqmc_trial* trial, const pqmc_opts* opts, pqmc_ctx** out);
+
+/* Same for a batch of n chains with their own specs (uneven sizes allowed):
+ * chain c follows specs[c] and uses Philox chain index chain_offset + c.
+ * opts->n_chains is ignored. */
+pqmc_status pqmc_init_batch(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts,
+                            pqmc_ctx** out);
+
+/* Enqueue n_sweeps sweeps of every chain on the context's stream
+ * (asynchronous). measure != 0 records one measurement per sweep and chain. */
+pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure);
+
+/* Wait for the context's stream and report any device-side error. */
+pqmc_status pqmc_synchronize(pqmc_ctx* ctx);
+
+/* Estimates for one chain (chain >= 0) or pooled over all chains (chain = -1,
+ * meaningful when the chains share one spec). Synchronises first. */
+pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out);
+
+/* Raw per-sweep records of one chain: out[m*5 + {0..4}] = (sign of the weight
+ * from the stabilised stacks, E/site, docc/site, kinetic energy/site, running
+ * product of sgn(R) over accepted flips) for m < *n; on entry *n is the
+ * capacity in records, on return the number written. Synchronises first. */
+pqmc_status pqmc_get_measurements(pqmc_ctx* ctx, int chain, double* out, long* n);
+
+/* Replace the fields of one chain ((Ltau+2) x N int8, values +-1) and rebuild its
+ * stacks and G as at initialisation. Allowed only when an even number of
+ * sweeps has been run (the next sweep goes up). */
+pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields);
+pqmc_status pqmc_get_fields(pqmc_ctx* ctx, int chain, int8_t* fields);
+
+/* Current G of one chain and spin as FP64 N x N (after an even number of
+ * sweeps: G(tau = -1); after an odd number: G(tau = Ltau+1)). */
+pqmc_status pqmc_get_green(pqmc_ctx* ctx, int chain, int spin, double* out);
+
+/* log|det(B_L B_R)| and sign per spin at the last stabilisation of a chain:
+ * out[0..3] = (logabs_up, sign_up, logabs_dn, sign_dn). */
+pqmc_status pqmc_get_weight(pqmc_ctx* ctx, int chain, double* out);
+
+/* Accept bits (0/1) of the first n proposals of a chain in visiting order
+ * (requires opts.accept_log >= n). */
+pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);
+
+/* max |G - G_fresh| at each stabilisation, oldest first, up to *n values
+ * (in: capacity, out: written). The history keeps the last 4096 values. */
+pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n);
+
+/* Sizes of one chain: out[0..5] = (N, N_up, N_dn, Ltau, n_stab, delay_k). */
+pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out);
+
+/* Number of chains in the context, or -1 for NULL. */
+int pqmc_num_chains(const pqmc_ctx* ctx);
+
+/* Device kernels launched by this context so far (all entry points). */
+long pqmc_launch_count(const pqmc_ctx* ctx);
+
+/* Last error message of a context (or of the last failed pqmc_init* call when
+ * ctx is NULL). Never NULL. */
+const char* pqmc_last_error(const pqmc_ctx* ctx);
+
+/* Release the context and its device memory. NULL is allowed. */
+void pqmc_free(pqmc_ctx* ctx);
+
+/* Host-side model set-up, exposed for tests (no GPU needed). Builds the
+ * hopping matrix K (N x N, row-major) of a lattice, e^{sign_x * dtau K}
+ * (dtau < 0 gives e^{+|dtau| K}) and the trial orbitals of one spin
+ * (spin 0 up, 1 down; N x n_sigma, row-major) from the library's own FP64
+ * symmetric eigensolver. Any output pointer may be NULL. gap receives the
+ * gap above the last occupied trial level. */
+pqmc_status pqmc_host_model(const pqmc_lattice* lattice, double dtau, const pqmc_trial* trial,
+                            int spin, double* K, double* expK, double* P, double* gap);
+
+/* Library's own FP64 symmetric eigensolver (Householder tridiagonalisation +
+ * implicit QL with Wilkinson shifts): A is n x n row-major symmetric;
+ * eigenvalues ascending into w, eigenvectors as columns of V (row-major).
+ * Exposed for tests. */
+pqmc_status pqmc_host_eigh(int n, const double* A, double* w, double* V);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PQMC_H */

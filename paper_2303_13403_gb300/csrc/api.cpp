@@ -1,0 +1,647 @@
+// C-ABI of libpqmc.so (declarations and documentation in include/pqmc.h).
+//
+// Host side: validates the chain specs, builds the model in FP64 (model.cpp),
+// draws the initial fields with Philox, lays out one device arena per context
+// and drives the kernels of sweep.cu on the context's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pqmc.h"
+#include "chain.h"
+#include "model.h"
+#include "philox.cuh"
+
+namespace pqmc {
+size_t smem_bytes(int prec);
+cudaError_t launch_init(int prec, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, int* d_err,
+                        cudaStream_t stream);
+cudaError_t launch_sweep(int prec, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0, int n_sweeps,
+                         int measure, int* d_err, cudaStream_t stream);
+}  // namespace pqmc
+
+using namespace pqmc;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct HostChain {
+  pqmc_chain_spec spec;
+  int N, ld, nup, ndn, nmax, Ltau, nb;
+  size_t off_fields, off_G, off_Gt, off_Rst, off_Lst, off_Rlog, off_Llog, off_work, off_UW, off_meas, off_dG,
+      off_acc, off_state, off_P, off_expKm, off_expKp, off_expKm64, off_K64;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct pqmc_ctx {
+  pqmc_opts opts;
+  int prec = 0;
+  size_t tsize = 8;
+  std::vector<HostChain> chains;
+  std::vector<ChainDesc> desc;
+  std::vector<unsigned char> host_arena;   // initial contents of the device arena
+  unsigned char* d_arena = nullptr;
+  size_t arena_bytes = 0;
+  ChainDesc* d_desc = nullptr;
+  int* d_err = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t sweep_index = 0;
+  long launches = 0;
+  int sticky = PQMC_OK;
+  std::string err;
+};
+
+namespace {
+
+pqmc_status fail(pqmc_ctx* ctx, pqmc_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg; else g_init_error = msg;
+  return st;
+}
+
+pqmc_status cuda_fail(pqmc_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, PQMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int n_sites(const pqmc_lattice& l) { return l.kind == PQMC_HONEYCOMB ? 2 * l.Lx * l.Ly : l.Lx * l.Ly; }
+
+// model tables shared by chains with the same lattice and dtau
+struct ModelTables {
+  std::vector<double> K, eps, w, V, expKm, expKp;
+};
+
+std::string lattice_key(const pqmc_chain_spec& s) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%d/%d/%d/%.17g/%.17g/%.17g", s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t,
+           s.lattice.tp, s.dtau);
+  return buf;
+}
+
+pqmc_status check_spec(const pqmc_chain_spec& s, const pqmc_opts& o, std::string& why) {
+  const auto& l = s.lattice;
+  if (l.kind != PQMC_HONEYCOMB && l.kind != PQMC_SQUARE) { why = "unknown lattice kind"; return PQMC_EINVAL; }
+  if (l.Lx < 1 || l.Ly < 1 || l.Lx > 64 || l.Ly > 64) { why = "lattice extent out of range"; return PQMC_EINVAL; }
+  const int N = n_sites(l);
+  if (N > 2048) { why = "more than 2048 sites"; return PQMC_EINVAL; }
+  const int nup = s.trial.N_up < 0 ? N / 2 : s.trial.N_up;
+  const int ndn = s.trial.N_dn < 0 ? N / 2 : s.trial.N_dn;
+  if (nup < 1 || ndn < 1 || nup > N || ndn > N) { why = "N_sigma must be in 1..N"; return PQMC_EINVAL; }
+  if (nup > 1024 || ndn > 1024) { why = "N_sigma above 1024"; return PQMC_EINVAL; }
+  if (!(s.dtau > 0) || !(s.two_theta >= 0) || !std::isfinite(s.U) || s.U < 0) {
+    why = "need dtau > 0, two_theta >= 0, U >= 0"; return PQMC_EINVAL;
+  }
+  if (!(s.trial.g >= 0) || !std::isfinite(s.trial.M_N)) { why = "need g >= 0 and finite M_N"; return PQMC_EINVAL; }
+  const double lt = s.two_theta / s.dtau;
+  const int Ltau = (int)std::lround(lt);
+  if (std::fabs(lt - Ltau) > 1e-9 * std::max(1.0, lt)) { why = "two_theta / dtau is not an integer"; return PQMC_EINVAL; }
+  if (Ltau % 2) { why = "Ltau must be even"; return PQMC_EINVAL; }
+  if (o.n_stab < 1 || (Ltau / 2) % o.n_stab) { why = "Ltau/2 must be a multiple of n_stab"; return PQMC_EINVAL; }
+  return PQMC_OK;
+}
+
+template <typename T>
+void put(std::vector<unsigned char>& a, size_t off, const std::vector<double>& src, int rows, int cols, int ld) {
+  T* p = reinterpret_cast<T*>(a.data() + off);
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) p[(size_t)i * ld + j] = (T)src[(size_t)i * cols + j];
+}
+
+void put_raw(std::vector<unsigned char>& a, size_t off, const void* src, size_t n) {
+  memcpy(a.data() + off, src, n);
+}
+
+pqmc_status sync_check(pqmc_ctx* ctx) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  int herr = 0;
+  e = cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "error word copy");
+  if (herr) {
+    if (herr & kErrTimeout) ctx->sticky = PQMC_ETIMEOUT;
+    else if (herr & kErrNaN) ctx->sticky = PQMC_ENAN;
+    else ctx->sticky = PQMC_ESTAB;
+    ctx->err = (herr & kErrNaN) ? "NaN or Inf in a ratio or in G" :
+               (herr & kErrStab) ? "singular matrix in the stabilisation" : "device wait timed out";
+    return (pqmc_status)ctx->sticky;
+  }
+  return PQMC_OK;
+}
+
+pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_ctx** out) {
+  if (!out) return fail(nullptr, PQMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !specs || !opts) return fail(nullptr, PQMC_EINVAL, "need n >= 1, specs and opts");
+  pqmc_opts o = *opts;
+  if (o.prec < PQMC_FP64 || o.prec > PQMC_BF16X3) return fail(nullptr, PQMC_EINVAL, "unknown precision");
+  if (o.prec == PQMC_BF16X3) return fail(nullptr, PQMC_EINVAL, "BF16X3 path not available in this build");
+  if (o.delay_k == 0) o.delay_k = kBlock;
+  if (o.delay_k != kBlock) return fail(nullptr, PQMC_EINVAL, "delay_k must be 0 or 32");
+  if (o.max_meas <= 0) o.max_meas = 4096;
+  if (o.accept_log < 0) return fail(nullptr, PQMC_EINVAL, "accept_log < 0");
+  for (int c = 0; c < n; ++c) {
+    std::string why;
+    if (check_spec(specs[c], o, why) != PQMC_OK) return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
+  }
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+    return fail(nullptr, PQMC_ECUDA, "no CUDA device");
+
+  auto* ctx = new pqmc_ctx();
+  ctx->opts = o;
+  ctx->prec = o.prec;
+  ctx->tsize = o.prec == PQMC_FP64 ? 8 : 4;
+
+  // ---- host model set-up and arena layout
+  std::map<std::string, ModelTables> models;
+  std::map<std::string, size_t> model_off;   // offset of expKm (T) for the lattice key
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
+  ctx->chains.resize(n);
+  struct TrialOut { std::vector<double> P[2]; };
+  std::vector<TrialOut> trials(n);
+  for (int c = 0; c < n; ++c) {
+    const pqmc_chain_spec& s = specs[c];
+    HostChain& h = ctx->chains[c];
+    h.spec = s;
+    h.N = n_sites(s.lattice);
+    h.ld = (int)align_up(h.N, 4);
+    h.nup = s.trial.N_up < 0 ? h.N / 2 : s.trial.N_up;
+    h.ndn = s.trial.N_dn < 0 ? h.N / 2 : s.trial.N_dn;
+    h.nmax = std::max(h.nup, h.ndn);
+    h.Ltau = (int)std::lround(s.two_theta / s.dtau);
+    h.nb = h.Ltau / o.n_stab;
+    const std::string key = lattice_key(s);
+    if (!models.count(key)) {
+      ModelTables mt;
+      Lattice lat{s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t, s.lattice.tp};
+      build_hopping(lat, mt.K, mt.eps);
+      if (!sym_eig(h.N, mt.K, mt.w, mt.V)) { delete ctx; return fail(nullptr, PQMC_EINVAL, "eigensolver failed on K"); }
+      expm_from_eig(h.N, mt.w, mt.V, -s.dtau, mt.expKm);
+      expm_from_eig(h.N, mt.w, mt.V, +s.dtau, mt.expKp);
+      models[key] = std::move(mt);
+      const size_t Tm = (size_t)h.N * h.ld * ctx->tsize;
+      const size_t o1 = take(Tm);
+      take(Tm);
+      take((size_t)h.N * h.N * 8);
+      take((size_t)h.N * h.N * 8);
+      model_off[key] = o1;
+    }
+    const ModelTables& mt = models[key];
+    Lattice lat{s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t, s.lattice.tp};
+    for (int sp = 0; sp < 2; ++sp) {
+      double gap = 0;
+      if (!trial_orbitals(lat, mt.K, mt.eps, s.trial.M_N, s.trial.tiebreak, sp == 0 ? 1 : -1,
+                          sp == 0 ? h.nup : h.ndn, trials[c].P[sp], gap)) {
+        delete ctx; return fail(nullptr, PQMC_EINVAL, "eigensolver failed on the trial Hamiltonian");
+      }
+      if (!(gap > 1e-8)) {
+        delete ctx;
+        return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": open-shell trial (gap " + std::to_string(gap) + ")");
+      }
+    }
+    h.off_expKm = model_off[key];
+    h.off_expKp = h.off_expKm + align_up((size_t)h.N * h.ld * ctx->tsize, 256);
+    h.off_expKm64 = h.off_expKp + align_up((size_t)h.N * h.ld * ctx->tsize, 256);
+    h.off_K64 = h.off_expKm64 + align_up((size_t)h.N * h.N * 8, 256);
+    const size_t Gbytes = 2ull * h.N * h.ld * ctx->tsize;
+    const size_t blk = (size_t)h.N * h.nmax * 8;
+    h.off_fields = take((size_t)(h.Ltau + 2) * h.N);
+    h.off_G = take(Gbytes);
+    h.off_Gt = take(Gbytes);
+    h.off_P = take(2 * blk);
+    h.off_Rst = take((size_t)(h.nb + 1) * 2 * blk);
+    h.off_Lst = take((size_t)(h.nb + 1) * 2 * blk);
+    h.off_Rlog = take((size_t)(h.nb + 1) * 4 * 8);
+    h.off_Llog = take((size_t)(h.nb + 1) * 4 * 8);
+    h.off_work = take((2ull * h.N * h.nmax + (size_t)h.nmax * h.nmax + (size_t)h.nmax * h.N) * 8);
+    h.off_UW = take((2ull * h.N * kBlock + 2ull * kBlock * h.ld) * ctx->tsize);
+    h.off_meas = take((size_t)o.max_meas * kRecord * 8);
+    h.off_dG = take((size_t)kDGHistory * 8);
+    h.off_acc = take((size_t)std::max(o.accept_log, 1));
+    h.off_state = take(sizeof(ChainState));
+  }
+  ctx->arena_bytes = off;
+
+  // ---- initial arena contents
+  ctx->host_arena.assign(off, 0);
+  auto& A = ctx->host_arena;
+  std::map<std::string, bool> written;
+  for (int c = 0; c < n; ++c) {
+    HostChain& h = ctx->chains[c];
+    const pqmc_chain_spec& s = h.spec;
+    const std::string key = lattice_key(s);
+    if (!written[key]) {
+      const ModelTables& mt = models[key];
+      if (ctx->prec == PQMC_FP64) {
+        put<double>(A, h.off_expKm, mt.expKm, h.N, h.N, h.ld);
+        put<double>(A, h.off_expKp, mt.expKp, h.N, h.N, h.ld);
+      } else {
+        put<float>(A, h.off_expKm, mt.expKm, h.N, h.N, h.ld);
+        put<float>(A, h.off_expKp, mt.expKp, h.N, h.N, h.ld);
+      }
+      put<double>(A, h.off_expKm64, mt.expKm, h.N, h.N, h.N);
+      put<double>(A, h.off_K64, mt.K, h.N, h.N, h.N);
+      written[key] = true;
+    }
+    // P_sigma column-major (ld N) in blocks of N x nmax
+    double* P = reinterpret_cast<double*>(A.data() + h.off_P);
+    for (int sp = 0; sp < 2; ++sp) {
+      const int ns = sp == 0 ? h.nup : h.ndn;
+      for (int i = 0; i < h.N; ++i)
+        for (int k = 0; k < ns; ++k) P[(size_t)sp * h.N * h.nmax + (size_t)k * h.N + i] = trials[c].P[sp][(size_t)i * ns + k];
+    }
+    int8_t* F = reinterpret_cast<int8_t*>(A.data() + h.off_fields);
+    const uint32_t chain_index = (uint32_t)(o.chain_offset + c);
+    for (int t = 0; t < h.Ltau + 2; ++t)
+      for (int i = 0; i < h.N; ++i) F[(size_t)t * h.N + i] = (int8_t)initial_field(o.seed, chain_index, t, i);
+    ChainState st{};
+    st.sign_running = 1.0;
+    st.logw[0][1] = st.logw[1][1] = 1.0;
+    put_raw(A, h.off_state, &st, sizeof st);
+  }
+
+  // ---- device
+  cudaError_t e;
+  if (o.stream) {
+    ctx->stream = (cudaStream_t)o.stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(nullptr, e, "stream create"); }
+    ctx->own_stream = true;
+  }
+  e = cudaMalloc(&ctx->d_arena, ctx->arena_bytes);
+  if (e != cudaSuccess) { pqmc_free(ctx); return fail(nullptr, PQMC_ENOMEM, std::string("device arena: ") + cudaGetErrorString(e)); }
+  e = cudaMalloc(&ctx->d_desc, sizeof(ChainDesc) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
+  if (e != cudaSuccess) { pqmc_free(ctx); return fail(nullptr, PQMC_ENOMEM, "device descriptors"); }
+  ctx->desc.resize(n);
+  for (int c = 0; c < n; ++c) {
+    HostChain& h = ctx->chains[c];
+    const pqmc_chain_spec& s = h.spec;
+    ChainDesc& d = ctx->desc[c];
+    memset(&d, 0, sizeof d);
+    d.N = h.N; d.ld = h.ld; d.nup = h.nup; d.ndn = h.ndn; d.nmax = h.nmax;
+    d.Ltau = h.Ltau; d.nb = h.nb; d.n_stab = o.n_stab; d.kb = o.delay_k;
+    d.chain_index = (uint32_t)(o.chain_offset + c);
+    d.U = s.U;
+    const double kap[2] = {hs_coupling(s.dtau * s.U), hs_coupling(s.trial.g)};
+    for (int k = 0; k < 2; ++k)
+      for (int sp = 0; sp < 2; ++sp)
+        for (int si = 0; si < 2; ++si) {
+          const double sigma = sp == 0 ? 1.0 : -1.0, sv = si == 0 ? 1.0 : -1.0;
+          d.delta[k][sp][si] = std::exp(-2.0 * sigma * kap[k] * sv) - 1.0;
+          d.vexp[k][sp][si] = std::exp(sigma * kap[k] * sv);
+        }
+    unsigned char* b = ctx->d_arena;
+    d.fields = reinterpret_cast<int8_t*>(b + h.off_fields);
+    d.G = b + h.off_G;
+    d.Gt = b + h.off_Gt;
+    d.expKm = b + h.off_expKm;
+    d.expKp = b + h.off_expKp;
+    d.expKm64 = reinterpret_cast<const double*>(b + h.off_expKm64);
+    d.K64 = reinterpret_cast<const double*>(b + h.off_K64);
+    d.P = reinterpret_cast<const double*>(b + h.off_P);
+    d.Rst = reinterpret_cast<double*>(b + h.off_Rst);
+    d.Lst = reinterpret_cast<double*>(b + h.off_Lst);
+    d.Rlog = reinterpret_cast<double*>(b + h.off_Rlog);
+    d.Llog = reinterpret_cast<double*>(b + h.off_Llog);
+    d.work = reinterpret_cast<double*>(b + h.off_work);
+    d.UW = b + h.off_UW;
+    d.meas = reinterpret_cast<double*>(b + h.off_meas);
+    d.max_meas = o.max_meas;
+    d.dG = reinterpret_cast<double*>(b + h.off_dG);
+    d.acc_log = reinterpret_cast<uint8_t*>(b + h.off_acc);
+    d.acc_cap = o.accept_log;
+    d.st = reinterpret_cast<ChainState*>(b + h.off_state);
+  }
+  e = cudaMemcpyAsync(ctx->d_arena, A.data(), ctx->arena_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+  if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
+  e = launch_init(ctx->prec, ctx->d_desc, 0, n, o.seed, ctx->d_err, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "init launch"); }
+  pqmc_status st = sync_check(ctx);
+  if (st != PQMC_OK) { g_init_error = ctx->err; pqmc_free(ctx); return st; }
+  *out = ctx;
+  return PQMC_OK;
+}
+
+bool chain_ok(pqmc_ctx* ctx, int chain) { return ctx && chain >= 0 && chain < (int)ctx->chains.size(); }
+
+pqmc_status read_state(pqmc_ctx* ctx, int chain, ChainState& st) {
+  cudaError_t e = cudaMemcpy(&st, ctx->desc[chain].st, sizeof st, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "state copy");
+}
+
+pqmc_status read_records(pqmc_ctx* ctx, int chain, std::vector<double>& rec, int& n) {
+  ChainState st;
+  pqmc_status s = read_state(ctx, chain, st);
+  if (s != PQMC_OK) return s;
+  n = std::min(st.n_meas, ctx->opts.max_meas);
+  rec.resize((size_t)n * kRecord);
+  if (n == 0) return PQMC_OK;
+  cudaError_t e = cudaMemcpy(rec.data(), ctx->desc[chain].meas, rec.size() * 8, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "record copy");
+}
+
+// ratio estimate sum(s O)/sum(s) with a jackknife over the given groups
+void estimate(const std::vector<std::vector<double>>& groups_sO, const std::vector<std::vector<double>>& groups_s,
+              double& mean, double& err) {
+  const size_t nb = groups_s.size();
+  std::vector<double> so(nb, 0.0), ss(nb, 0.0);
+  double tso = 0, tss = 0;
+  for (size_t b = 0; b < nb; ++b) {
+    for (double v : groups_sO[b]) so[b] += v;
+    for (double v : groups_s[b]) ss[b] += v;
+    tso += so[b];
+    tss += ss[b];
+  }
+  mean = tso / tss;
+  if (nb < 2) { err = NAN; return; }
+  std::vector<double> jk(nb);
+  double m = 0;
+  for (size_t b = 0; b < nb; ++b) { jk[b] = (tso - so[b]) / (tss - ss[b]); m += jk[b]; }
+  m /= nb;
+  double v = 0;
+  for (size_t b = 0; b < nb; ++b) v += (jk[b] - m) * (jk[b] - m);
+  err = std::sqrt((double)(nb - 1) / nb * v);
+}
+
+}  // namespace
+
+extern "C" {
+
+pqmc_status pqmc_init(const pqmc_lattice* lattice, double U, double dtau, double two_theta, const pqmc_trial* trial,
+                      const pqmc_opts* opts, pqmc_ctx** out) {
+  if (!lattice || !trial || !opts) return fail(nullptr, PQMC_EINVAL, "NULL argument");
+  if (opts->n_chains < 1) return fail(nullptr, PQMC_EINVAL, "n_chains must be >= 1");
+  std::vector<pqmc_chain_spec> specs(opts->n_chains);
+  for (auto& s : specs) {
+    s.lattice = *lattice;
+    s.U = U;
+    s.dtau = dtau;
+    s.two_theta = two_theta;
+    s.trial = *trial;
+  }
+  return build_ctx(opts->n_chains, specs.data(), opts, out);
+}
+
+pqmc_status pqmc_init_batch(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_ctx** out) {
+  return build_ctx(n, specs, opts, out);
+}
+
+pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
+  if (!ctx || n_sweeps < 0) return PQMC_EINVAL;
+  if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
+  if (n_sweeps == 0) return PQMC_OK;
+  cudaError_t e = launch_sweep(ctx->prec, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed, ctx->sweep_index,
+                               n_sweeps, measure, ctx->d_err, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
+  ctx->sweep_index += (uint32_t)n_sweeps;
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_synchronize(pqmc_ctx* ctx) {
+  if (!ctx) return PQMC_EINVAL;
+  return sync_check(ctx);
+}
+
+pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
+  if (!ctx || !out || chain < -1 || chain >= (int)ctx->chains.size()) return PQMC_EINVAL;
+  pqmc_status s = sync_check(ctx);
+  if (s != PQMC_OK) return s;
+  const int c0 = chain < 0 ? 0 : chain, c1 = chain < 0 ? (int)ctx->chains.size() : chain + 1;
+  std::vector<std::vector<double>> gs, gE, gD;
+  long long prop = 0, acc = 0;
+  double maxdG = 0;
+  long nm = 0;
+  std::vector<std::vector<double>> per_s, per_E, per_D;
+  for (int c = c0; c < c1; ++c) {
+    std::vector<double> rec;
+    int n = 0;
+    if ((s = read_records(ctx, c, rec, n)) != PQMC_OK) return s;
+    ChainState st;
+    if ((s = read_state(ctx, c, st)) != PQMC_OK) return s;
+    prop += st.n_prop;
+    acc += st.n_acc;
+    maxdG = std::max(maxdG, st.max_dG);
+    nm += n;
+    std::vector<double> sv(n), Ev(n), Dv(n);
+    for (int m = 0; m < n; ++m) {
+      sv[m] = rec[(size_t)m * kRecord + 0];
+      Ev[m] = sv[m] * rec[(size_t)m * kRecord + 1];
+      Dv[m] = sv[m] * rec[(size_t)m * kRecord + 2];
+    }
+    per_s.push_back(sv);
+    per_E.push_back(Ev);
+    per_D.push_back(Dv);
+  }
+  // groups: chains when pooling several, else up to 20 bins of consecutive sweeps
+  std::vector<std::vector<double>> bs, bE, bD;
+  if (per_s.size() >= 2) {
+    bs = per_s; bE = per_E; bD = per_D;
+  } else if (!per_s.empty()) {
+    const int n = (int)per_s[0].size();
+    const int nbins = std::max(1, std::min(n, 20));
+    const int per = std::max(1, n / nbins);
+    for (int b = 0; b < nbins && (b + 1) * per <= n; ++b) {
+      bs.emplace_back(per_s[0].begin() + b * per, per_s[0].begin() + (b + 1) * per);
+      bE.emplace_back(per_E[0].begin() + b * per, per_E[0].begin() + (b + 1) * per);
+      bD.emplace_back(per_D[0].begin() + b * per, per_D[0].begin() + (b + 1) * per);
+    }
+  }
+  memset(out, 0, sizeof *out);
+  out->n_meas = nm;
+  out->accept = prop ? (double)acc / prop : 0.0;
+  out->max_dG = maxdG;
+  if (nm == 0 || bs.empty()) {
+    out->E = out->E_err = out->docc = out->docc_err = out->sign = out->sign_err = NAN;
+    return PQMC_OK;
+  }
+  estimate(bE, bs, out->E, out->E_err);
+  estimate(bD, bs, out->docc, out->docc_err);
+  // average sign: mean of s with the same grouping
+  std::vector<std::vector<double>> ones;
+  for (auto& g : bs) ones.emplace_back(g.size(), 1.0);
+  estimate(bs, ones, out->sign, out->sign_err);
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_get_measurements(pqmc_ctx* ctx, int chain, double* out, long* n) {
+  if (!chain_ok(ctx, chain) || !out || !n || *n < 0) return PQMC_EINVAL;
+  pqmc_status s = sync_check(ctx);
+  if (s != PQMC_OK && s != PQMC_ENAN && s != PQMC_ESTAB) return s;
+  std::vector<double> rec;
+  int m = 0;
+  if ((s = read_records(ctx, chain, rec, m)) != PQMC_OK) return s;
+  const long k = std::min<long>(*n, m);
+  memcpy(out, rec.data(), (size_t)k * kRecord * 8);
+  *n = k;
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields) {
+  if (!chain_ok(ctx, chain) || !fields) return PQMC_EINVAL;
+  if (ctx->sweep_index & 1u) return fail(ctx, PQMC_EINVAL, "set_fields needs an even number of sweeps done");
+  if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
+  const HostChain& h = ctx->chains[chain];
+  const size_t nf = (size_t)(h.Ltau + 2) * h.N;
+  for (size_t i = 0; i < nf; ++i)
+    if (fields[i] != 1 && fields[i] != -1) return fail(ctx, PQMC_EINVAL, "fields must be +1 or -1");
+  cudaError_t e = cudaMemcpyAsync(ctx->desc[chain].fields, fields, nf, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
+  e = launch_init(ctx->prec, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->d_err, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "init launch");
+  return sync_check(ctx);
+}
+
+pqmc_status pqmc_get_fields(pqmc_ctx* ctx, int chain, int8_t* fields) {
+  if (!chain_ok(ctx, chain) || !fields) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  const HostChain& h = ctx->chains[chain];
+  e = cudaMemcpy(fields, ctx->desc[chain].fields, (size_t)(h.Ltau + 2) * h.N, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "fields copy");
+}
+
+pqmc_status pqmc_get_green(pqmc_ctx* ctx, int chain, int spin, double* out) {
+  if (!chain_ok(ctx, chain) || !out || spin < 0 || spin > 1) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  const HostChain& h = ctx->chains[chain];
+  const size_t cnt = (size_t)h.N * h.ld;
+  std::vector<unsigned char> buf(cnt * ctx->tsize);
+  e = cudaMemcpy(buf.data(), (unsigned char*)ctx->desc[chain].G + spin * cnt * ctx->tsize, buf.size(),
+                 cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "G copy");
+  for (int i = 0; i < h.N; ++i)
+    for (int j = 0; j < h.N; ++j) {
+      const size_t k = (size_t)i * h.ld + j;
+      out[(size_t)i * h.N + j] = ctx->tsize == 8 ? reinterpret_cast<double*>(buf.data())[k]
+                                                 : (double)reinterpret_cast<float*>(buf.data())[k];
+    }
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_get_weight(pqmc_ctx* ctx, int chain, double* out) {
+  if (!chain_ok(ctx, chain) || !out) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  ChainState st;
+  pqmc_status s = read_state(ctx, chain, st);
+  if (s != PQMC_OK) return s;
+  out[0] = st.logw[0][0]; out[1] = st.logw[0][1];
+  out[2] = st.logw[1][0]; out[3] = st.logw[1][1];
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n) {
+  if (!chain_ok(ctx, chain) || !out || n < 0 || n > ctx->opts.accept_log) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  if (n == 0) return PQMC_OK;
+  e = cudaMemcpy(out, ctx->desc[chain].acc_log, (size_t)n, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "accept log copy");
+}
+
+pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n) {
+  if (!chain_ok(ctx, chain) || !out || !n || *n < 0) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  ChainState st;
+  pqmc_status s = read_state(ctx, chain, st);
+  if (s != PQMC_OK) return s;
+  std::vector<double> ring(kDGHistory);
+  e = cudaMemcpy(ring.data(), ctx->desc[chain].dG, kDGHistory * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dG copy");
+  const long total = st.n_dG;
+  const long kept = std::min<long>(total, kDGHistory);
+  const long k = std::min<long>(*n, kept);
+  const long first = total - kept;
+  for (long m = 0; m < k; ++m) out[m] = ring[(first + m) % kDGHistory];
+  *n = k;
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out) {
+  if (!chain_ok(ctx, chain) || !out) return PQMC_EINVAL;
+  const HostChain& h = ctx->chains[chain];
+  out[0] = h.N; out[1] = h.nup; out[2] = h.ndn; out[3] = h.Ltau; out[4] = ctx->opts.n_stab; out[5] = ctx->opts.delay_k;
+  return PQMC_OK;
+}
+
+int pqmc_num_chains(const pqmc_ctx* ctx) { return ctx ? (int)ctx->chains.size() : -1; }
+
+long pqmc_launch_count(const pqmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* pqmc_last_error(const pqmc_ctx* ctx) {
+  if (!ctx) return g_init_error.c_str();
+  return ctx->err.c_str();
+}
+
+void pqmc_free(pqmc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->d_arena) cudaFree(ctx->d_arena);
+  if (ctx->d_desc) cudaFree(ctx->d_desc);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+pqmc_status pqmc_host_model(const pqmc_lattice* lattice, double dtau, const pqmc_trial* trial, int spin, double* K,
+                            double* expK, double* P, double* gap) {
+  if (!lattice || spin < 0 || spin > 1) return fail(nullptr, PQMC_EINVAL, "bad argument");
+  if (lattice->Lx < 1 || lattice->Ly < 1 || lattice->Lx > 64 || lattice->Ly > 64 ||
+      (lattice->kind != 0 && lattice->kind != 1))
+    return fail(nullptr, PQMC_EINVAL, "bad lattice");
+  Lattice lat{lattice->kind, lattice->Lx, lattice->Ly, lattice->t, lattice->tp};
+  const int N = lat.n_sites();
+  std::vector<double> Km, eps, w, V, E;
+  build_hopping(lat, Km, eps);
+  if (K) memcpy(K, Km.data(), Km.size() * 8);
+  if (expK) {
+    if (!sym_eig(N, Km, w, V)) return fail(nullptr, PQMC_EINVAL, "eigensolver failed");
+    expm_from_eig(N, w, V, -dtau, E);
+    memcpy(expK, E.data(), E.size() * 8);
+  }
+  if (P || gap) {
+    if (!trial) return fail(nullptr, PQMC_EINVAL, "trial is NULL");
+    const int ns = spin == 0 ? (trial->N_up < 0 ? N / 2 : trial->N_up) : (trial->N_dn < 0 ? N / 2 : trial->N_dn);
+    if (ns < 1 || ns > N) return fail(nullptr, PQMC_EINVAL, "bad N_sigma");
+    std::vector<double> Pm;
+    double g = 0;
+    if (!trial_orbitals(lat, Km, eps, trial->M_N, trial->tiebreak, spin == 0 ? 1 : -1, ns, Pm, g))
+      return fail(nullptr, PQMC_EINVAL, "eigensolver failed");
+    if (P) memcpy(P, Pm.data(), Pm.size() * 8);
+    if (gap) *gap = g;
+  }
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_host_eigh(int n, const double* A, double* w, double* V) {
+  if (n < 1 || !A || !w || !V) return fail(nullptr, PQMC_EINVAL, "bad argument");
+  std::vector<double> Am(A, A + (size_t)n * n), wm, Vm;
+  if (!sym_eig(n, Am, wm, Vm)) return fail(nullptr, PQMC_EINVAL, "eigensolver did not converge");
+  memcpy(w, wm.data(), (size_t)n * 8);
+  memcpy(V, Vm.data(), (size_t)n * n * 8);
+  return PQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""ctypes binding of libpqmc.so (argument marshalling only).
+
+Every entry point of ``include/pqmc.h`` is reachable under the same name.
+Nothing here computes any step of the sweep: the library does, on the GPU.
+``load()`` raises when the library has not been built; there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpqmc.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTAB, ENAN, ETIMEOUT = range(7)
+STATUS = {0: "PQMC_OK", 1: "PQMC_EINVAL", 2: "PQMC_ENOMEM", 3: "PQMC_ECUDA", 4: "PQMC_ESTAB",
+          5: "PQMC_ENAN", 6: "PQMC_ETIMEOUT"}
+FP64, FP32, BF16X3 = 0, 1, 2
+HONEYCOMB, SQUARE = 0, 1
+
+
+class Lattice(C.Structure):
+    _fields_ = [("kind", C.c_int), ("Lx", C.c_int), ("Ly", C.c_int), ("t", C.c_double), ("tp", C.c_double)]
+
+
+class Trial(C.Structure):
+    _fields_ = [("g", C.c_double), ("M_N", C.c_double), ("N_up", C.c_int), ("N_dn", C.c_int),
+                ("tiebreak", C.c_double)]
+
+
+class ChainSpec(C.Structure):
+    _fields_ = [("lattice", Lattice), ("U", C.c_double), ("dtau", C.c_double), ("two_theta", C.c_double),
+                ("trial", Trial)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("n_stab", C.c_int), ("delay_k", C.c_int), ("prec", C.c_int), ("seed", C.c_uint64),
+                ("n_chains", C.c_int), ("chain_offset", C.c_int), ("accept_log", C.c_int),
+                ("max_meas", C.c_int), ("stream", C.c_void_p)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("E", C.c_double), ("E_err", C.c_double), ("docc", C.c_double), ("docc_err", C.c_double),
+                ("sign", C.c_double), ("sign_err", C.c_double), ("accept", C.c_double), ("max_dG", C.c_double),
+                ("n_meas", C.c_long)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = [
+    ("pqmc_init", C.c_int, [C.POINTER(Lattice), C.c_double, C.c_double, C.c_double, C.POINTER(Trial),
+                            C.POINTER(Opts), C.POINTER(C.c_void_p)]),
+    ("pqmc_init_batch", C.c_int, [C.c_int, C.POINTER(ChainSpec), C.POINTER(Opts), C.POINTER(C.c_void_p)]),
+    ("pqmc_sweep", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("pqmc_synchronize", C.c_int, [C.c_void_p]),
+    ("pqmc_measure", C.c_int, [C.c_void_p, C.c_int, C.POINTER(Obs)]),
+    ("pqmc_get_measurements", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+    ("pqmc_set_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int8)]),
+    ("pqmc_get_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int8)]),
+    ("pqmc_get_green", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    ("pqmc_get_weight", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    ("pqmc_get_accept_log", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), C.c_long]),
+    ("pqmc_get_stab_errors", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+    ("pqmc_get_dims", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    ("pqmc_num_chains", C.c_int, [C.c_void_p]),
+    ("pqmc_launch_count", C.c_long, [C.c_void_p]),
+    ("pqmc_last_error", C.c_char_p, [C.c_void_p]),
+    ("pqmc_free", None, [C.c_void_p]),
+    ("pqmc_host_model", C.c_int, [C.POINTER(Lattice), C.c_double, C.POINTER(Trial), C.c_int,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
+    ("pqmc_host_eigh", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+]
+
+
+def load(path=LIB_PATH):
+    """Load libpqmc.so; raises if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libpqmc.so is not built (%s); run paper_2303_13403_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PQMCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _check(st, ctx=None):
+    if st != OK:
+        msg = load().pqmc_last_error(ctx).decode()
+        raise PQMCError(st, msg)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def lattice_of(spec):
+    return Lattice(spec.kind, spec.Lx, spec.Ly, spec.t, spec.tp)
+
+
+def trial_of(spec):
+    return Trial(spec.g, spec.M_N, spec.n_up, spec.n_dn, spec.tiebreak)
+
+
+def chain_spec_of(spec):
+    return ChainSpec(lattice_of(spec), spec.U, spec.dtau, spec.two_theta, trial_of(spec))
+
+
+class Context:
+    """One libpqmc context: a batch of chains on the GPU."""
+
+    def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=0, chain_offset=0, accept_log=0,
+                 max_meas=0, stream=None):
+        lib = load()
+        specs = list(specs)
+        arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
+        opts = Opts(n_stab, delay_k, prec, seed, len(specs), chain_offset, accept_log, max_meas,
+                    C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        _check(lib.pqmc_init_batch(len(specs), arr, C.byref(opts), C.byref(h)))
+        self._h = h
+        self.specs = specs
+        self.prec = prec
+        self.n_chains = len(specs)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().pqmc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1, measure=True):
+        _check(load().pqmc_sweep(self._h, n, 1 if measure else 0), self._h)
+
+    def synchronize(self):
+        _check(load().pqmc_synchronize(self._h), self._h)
+
+    def measure(self, chain=-1):
+        o = Obs()
+        _check(load().pqmc_measure(self._h, chain, C.byref(o)), self._h)
+        return o.as_dict()
+
+    def dims(self, chain=0):
+        d = (C.c_int * 6)()
+        _check(load().pqmc_get_dims(self._h, chain, d), self._h)
+        return dict(zip(("N", "N_up", "N_dn", "Ltau", "n_stab", "delay_k"), list(d)))
+
+    def measurements(self, chain=0, cap=1 << 16):
+        out = np.zeros((cap, 5))
+        n = C.c_long(cap)
+        _check(load().pqmc_get_measurements(self._h, chain, _dptr(out), C.byref(n)), self._h)
+        return out[: n.value]
+
+    def green(self, chain=0, spin=0):
+        N = self.dims(chain)["N"]
+        out = np.zeros((N, N))
+        _check(load().pqmc_get_green(self._h, chain, spin, _dptr(out)), self._h)
+        return out
+
+    def weight(self, chain=0):
+        out = np.zeros(4)
+        _check(load().pqmc_get_weight(self._h, chain, _dptr(out)), self._h)
+        return out
+
+    def fields(self, chain=0):
+        d = self.dims(chain)
+        out = np.zeros((d["Ltau"] + 2, d["N"]), dtype=np.int8)
+        _check(load().pqmc_get_fields(self._h, chain, out.ctypes.data_as(C.POINTER(C.c_int8))), self._h)
+        return out
+
+    def set_fields(self, fields, chain=0):
+        f = np.ascontiguousarray(fields, dtype=np.int8)
+        _check(load().pqmc_set_fields(self._h, chain, f.ctypes.data_as(C.POINTER(C.c_int8))), self._h)
+
+    def accept_log(self, n, chain=0):
+        out = np.zeros(n, dtype=np.uint8)
+        _check(load().pqmc_get_accept_log(self._h, chain, out.ctypes.data_as(C.POINTER(C.c_uint8)), n), self._h)
+        return out
+
+    def stab_errors(self, chain=0, cap=4096):
+        out = np.zeros(cap)
+        n = C.c_long(cap)
+        _check(load().pqmc_get_stab_errors(self._h, chain, _dptr(out), C.byref(n)), self._h)
+        return out[: n.value]
+
+    def launch_count(self):
+        return int(load().pqmc_launch_count(self._h))
+
+
+def host_model(spec, spin=0):
+    """(K, e^{-dtau K}, P_spin, gap) from the library's host model set-up."""
+    lib = load()
+    N = spec.n_sites
+    ns = (N // 2 if spec.n_up < 0 else spec.n_up) if spin == 0 else (N // 2 if spec.n_dn < 0 else spec.n_dn)
+    K = np.zeros((N, N))
+    E = np.zeros((N, N))
+    P = np.zeros((N, ns))
+    gap = C.c_double()
+    lat = lattice_of(spec)
+    tr = trial_of(spec)
+    _check(lib.pqmc_host_model(C.byref(lat), spec.dtau, C.byref(tr), spin, _dptr(K), _dptr(E), _dptr(P),
+                               C.byref(gap)))
+    return K, E, P, gap.value
+
+
+def host_eigh(A):
+    lib = load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(lib.pqmc_host_eigh(n, _dptr(A), _dptr(w), _dptr(V)))
+    return w, V

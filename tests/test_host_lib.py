@@ -1,0 +1,99 @@
+"""CPU-only checks of libpqmc.so: it loads, exports every declared entry point,
+and its host-side FP64 model set-up (own eigensolver) matches numpy and the
+oracle.  No GPU compute is called."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice as olat, pqmc as opq, trial as otrial
+from paper_2303_13403_gb300 import build, pqmc, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lib():
+    if not os.path.exists(pqmc.LIB_PATH):
+        build.build()
+    return pqmc.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pqmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pqmc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert {n for n, _, _ in pqmc.SIGNATURES} == set(names)
+
+
+def test_init_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pqmc.PQMCError) as e:
+        pqmc.Context([workloads.PLAIN_18])
+    assert e.value.status == pqmc.ECUDA
+
+
+def test_invalid_specs_rejected_before_device(lib):
+    bad = [
+        workloads.honeycomb(3, two_theta=1.0),                  # Ltau = 10: Ltau/2 = 5 not a multiple of 10
+        workloads.honeycomb(3, two_theta=0.1),                  # Ltau odd
+        workloads.ChainSpec(Lx=3, Ly=3, n_up=19),               # N_sigma > N
+        workloads.ChainSpec(Lx=0, Ly=3),
+        workloads.ChainSpec(Lx=3, Ly=3, dtau=-0.1),
+        workloads.ChainSpec(Lx=3, Ly=3, g=-0.5),
+    ]
+    for s in bad:
+        with pytest.raises(pqmc.PQMCError) as e:
+            pqmc.Context([s])
+        assert e.value.status == pqmc.EINVAL, s
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (7, 2), (18, 3), (50, 4), (97, 5)])
+def test_host_eigensolver_matches_numpy(lib, n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    w, V = pqmc.host_eigh(A)
+    assert np.allclose(w, np.linalg.eigvalsh(A), atol=1e-11)
+    assert np.allclose(V.T @ V, np.eye(n), atol=1e-12)
+    assert np.allclose(V @ np.diag(w) @ V.T, A, atol=1e-11)
+
+
+@pytest.mark.parametrize("L", [3, 6, 9])
+def test_host_eigensolver_degenerate_lattice_spectrum(lib, L):
+    K, _ = olat.honeycomb(L, L)
+    w, V = pqmc.host_eigh(K)
+    assert np.allclose(w, np.linalg.eigvalsh(K), atol=1e-11)
+    assert np.allclose(V @ np.diag(w) @ V.T, K, atol=1e-11)
+
+
+@pytest.mark.parametrize("spec", [
+    workloads.PLAIN_18,
+    workloads.GUTZ_72[8.0],
+    workloads.DOPED_64[0.3],
+    workloads.honeycomb(9, g=0.5, M_N=0.12, two_theta=8.0),
+    workloads.ChainSpec(kind=workloads.SQUARE, Lx=2, Ly=4, tp=-0.2, n_up=3, n_dn=3, M_N=0.1),
+])
+def test_host_model_matches_oracle(lib, spec):
+    p = opq.Params(kind=spec.kind, Lx=spec.Lx, Ly=spec.Ly, t=spec.t, tp=spec.tp, U=spec.U, dtau=spec.dtau,
+                   two_theta=spec.two_theta, g=spec.g, M_N=spec.M_N, n_up=spec.n_up, n_dn=spec.n_dn,
+                   n_stab=1 if spec.n_slices % 2 == 0 and spec.n_slices // 2 % 10 else 10)
+    m = opq.Model(p)
+    for spin, sigma in ((0, 1), (1, -1)):
+        K, E, P, gap = pqmc.host_model(spec, spin)
+        assert np.array_equal(K, m.K)
+        assert np.allclose(E, m.expKm, atol=1e-13)
+        # same occupied subspace: projectors agree
+        Po = m.P[sigma]
+        assert np.allclose(P @ P.T, Po @ Po.T, atol=1e-9)
+        assert np.isclose(gap, m.gap[sigma], rtol=1e-8)
