@@ -117,6 +117,9 @@ typedef struct {
                                accept_log proposals per chain (test hook) */
     int max_meas;           /* capacity of per-sweep measurement records per chain (0 = 4096) */
     void* stream;           /* cudaStream_t to run on, or NULL for a library-owned stream */
+    int cta_threads;        /* threads of the CTA that runs one chain: 64, 128 or 256; 0 picks
+                               64 for FP64 and 128 otherwise. Smaller CTAs put more chains
+                               on one SM (FP64: 256/cta_threads per SM, others twice that) */
 } pqmc_opts;
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
@@ -165,6 +168,11 @@ pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out);
  * capacity in records, on return the number written. Synchronises first. */
 pqmc_status pqmc_get_measurements(pqmc_ctx* ctx, int chain, double* out, long* n);
 
+/* Latest measurement record of every chain in one device-to-host copy:
+ * out[c*5 + {0..4}] as in pqmc_get_measurements (n_chains x 5 doubles; NaN
+ * for a chain that has no record yet). Synchronises first. */
+pqmc_status pqmc_get_last_records(pqmc_ctx* ctx, double* out);
+
 /* Replace the fields of one chain ((Ltau+2) x N int8, values +-1) and rebuild its
  * stacks and G as at initialisation. Allowed only when an even number of
  * sweeps has been run (the next sweep goes up). */
@@ -187,11 +195,21 @@ pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);
  * (in: capacity, out: written). The history keeps the last 4096 values. */
 pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n);
 
+/* SM clock cycles one chain's CTA has spent, as seen by its thread 0, in
+ * each phase of its sweeps so far: out[0..7] = (flip decisions, delayed-update
+ * flushes, slice wrapping, stack slice products, Householder QR, G refresh
+ * from the stacks, measurement, total). */
+pqmc_status pqmc_get_phase_cycles(pqmc_ctx* ctx, int chain, long long* out);
+
 /* Sizes of one chain: out[0..5] = (N, N_up, N_dn, Ltau, n_stab, delay_k). */
 pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out);
 
 /* Number of chains in the context, or -1 for NULL. */
 int pqmc_num_chains(const pqmc_ctx* ctx);
+
+/* Bytes of device memory held by the context (uploaded from the host at
+ * creation), or 0 for NULL. */
+size_t pqmc_device_bytes(const pqmc_ctx* ctx);
 
 /* Device kernels launched by this context so far (all entry points). */
 long pqmc_launch_count(const pqmc_ctx* ctx);

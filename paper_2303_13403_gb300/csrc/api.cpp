@@ -19,11 +19,11 @@
 #include "philox.cuh"
 
 namespace pqmc {
-size_t smem_bytes(int prec);
-cudaError_t launch_init(int prec, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, int* d_err,
-                        cudaStream_t stream);
-cudaError_t launch_sweep(int prec, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0, int n_sweeps,
-                         int measure, int* d_err, cudaStream_t stream);
+size_t smem_resident_cap(int prec, int tpb);
+cudaError_t launch_init(int prec, int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,
+                        int* d_err, cudaStream_t stream);
+cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0,
+                         int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
 }  // namespace pqmc
 
 using namespace pqmc;
@@ -35,8 +35,8 @@ thread_local std::string g_init_error;
 struct HostChain {
   pqmc_chain_spec spec;
   int N, ld, nup, ndn, nmax, Ltau, nb;
-  size_t off_fields, off_G, off_Gt, off_Rst, off_Lst, off_Rlog, off_Llog, off_work, off_UW, off_meas, off_dG,
-      off_acc, off_state, off_P, off_expKm, off_expKp, off_expKm64, off_K64;
+  size_t off_fields, off_G, off_Rst, off_Lst, off_Rlog, off_Llog, off_meas, off_dG,
+      off_acc, off_state, off_P, off_scratch, off_expKm, off_expKp, off_expKm64, off_K64;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -54,6 +54,9 @@ struct pqmc_ctx {
   size_t arena_bytes = 0;
   ChainDesc* d_desc = nullptr;
   int* d_err = nullptr;
+  size_t off_last = 0;                     // n_chains x kRecord latest records
+  size_t res_bytes = 0;                    // shared memory offered for resident chains
+  int tpb = 256;                           // threads per chain CTA
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   uint32_t sweep_index = 0;
@@ -92,11 +95,11 @@ pqmc_status check_spec(const pqmc_chain_spec& s, const pqmc_opts& o, std::string
   if (l.kind != PQMC_HONEYCOMB && l.kind != PQMC_SQUARE) { why = "unknown lattice kind"; return PQMC_EINVAL; }
   if (l.Lx < 1 || l.Ly < 1 || l.Lx > 64 || l.Ly > 64) { why = "lattice extent out of range"; return PQMC_EINVAL; }
   const int N = n_sites(l);
-  if (N > 2048) { why = "more than 2048 sites"; return PQMC_EINVAL; }
+  if (N > kMaxN) { why = "more than 1024 sites"; return PQMC_EINVAL; }
   const int nup = s.trial.N_up < 0 ? N / 2 : s.trial.N_up;
   const int ndn = s.trial.N_dn < 0 ? N / 2 : s.trial.N_dn;
   if (nup < 1 || ndn < 1 || nup > N || ndn > N) { why = "N_sigma must be in 1..N"; return PQMC_EINVAL; }
-  if (nup > 1024 || ndn > 1024) { why = "N_sigma above 1024"; return PQMC_EINVAL; }
+  if (nup > kMaxSigma || ndn > kMaxSigma) { why = "N_sigma above 512"; return PQMC_EINVAL; }
   if (!(s.dtau > 0) || !(s.two_theta >= 0) || !std::isfinite(s.U) || s.U < 0) {
     why = "need dtau > 0, two_theta >= 0, U >= 0"; return PQMC_EINVAL;
   }
@@ -148,6 +151,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (o.delay_k != kBlock) return fail(nullptr, PQMC_EINVAL, "delay_k must be 0 or 32");
   if (o.max_meas <= 0) o.max_meas = 4096;
   if (o.accept_log < 0) return fail(nullptr, PQMC_EINVAL, "accept_log < 0");
+  if (o.cta_threads != 0 && o.cta_threads != 64 && o.cta_threads != 128 && o.cta_threads != 256)
+    return fail(nullptr, PQMC_EINVAL, "cta_threads must be 0, 64, 128 or 256");
   for (int c = 0; c < n; ++c) {
     std::string why;
     if (check_spec(specs[c], o, why) != PQMC_OK) return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
@@ -217,18 +222,27 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     const size_t blk = (size_t)h.N * h.nmax * 8;
     h.off_fields = take((size_t)(h.Ltau + 2) * h.N);
     h.off_G = take(Gbytes);
-    h.off_Gt = take(Gbytes);
     h.off_P = take(2 * blk);
     h.off_Rst = take((size_t)(h.nb + 1) * 2 * blk);
     h.off_Lst = take((size_t)(h.nb + 1) * 2 * blk);
     h.off_Rlog = take((size_t)(h.nb + 1) * 4 * 8);
     h.off_Llog = take((size_t)(h.nb + 1) * 4 * 8);
-    h.off_work = take((2ull * h.N * h.nmax + (size_t)h.nmax * h.nmax + (size_t)h.nmax * h.N) * 8);
-    h.off_UW = take((2ull * h.N * kBlock + 2ull * kBlock * h.ld) * ctx->tsize);
+    h.off_scratch = take(scratch_layout(h.N, h.ld, h.nmax, (int)ctx->tsize).total);
     h.off_meas = take((size_t)o.max_meas * kRecord * 8);
     h.off_dG = take((size_t)kDGHistory * 8);
     h.off_acc = take((size_t)std::max(o.accept_log, 1));
     h.off_state = take(sizeof(ChainState));
+  }
+  ctx->off_last = take((size_t)n * kRecord * 8);
+  // default CTA size (measured on GB300 at 72 sites): the FP64 path packs 4
+  // chains of 64 threads per SM, the reduced paths 4 chains of 128 threads
+  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : 128);
+  {
+    const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb);
+    for (const HostChain& h : ctx->chains) {
+      const size_t r = resident_bytes(h.N, h.ld, h.nmax, (int)ctx->tsize);
+      if (r <= cap && r > ctx->res_bytes) ctx->res_bytes = r;
+    }
   }
   ctx->arena_bytes = off;
 
@@ -264,6 +278,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     const uint32_t chain_index = (uint32_t)(o.chain_offset + c);
     for (int t = 0; t < h.Ltau + 2; ++t)
       for (int i = 0; i < h.N; ++i) F[(size_t)t * h.N + i] = (int8_t)initial_field(o.seed, chain_index, t, i);
+    double* last = reinterpret_cast<double*>(A.data() + ctx->off_last) + (size_t)c * kRecord;
+    for (int k = 0; k < kRecord; ++k) last[k] = NAN;
     ChainState st{};
     st.sign_running = 1.0;
     st.logw[0][1] = st.logw[1][1] = 1.0;
@@ -305,7 +321,6 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     unsigned char* b = ctx->d_arena;
     d.fields = reinterpret_cast<int8_t*>(b + h.off_fields);
     d.G = b + h.off_G;
-    d.Gt = b + h.off_Gt;
     d.expKm = b + h.off_expKm;
     d.expKp = b + h.off_expKp;
     d.expKm64 = reinterpret_cast<const double*>(b + h.off_expKm64);
@@ -315,9 +330,9 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.Lst = reinterpret_cast<double*>(b + h.off_Lst);
     d.Rlog = reinterpret_cast<double*>(b + h.off_Rlog);
     d.Llog = reinterpret_cast<double*>(b + h.off_Llog);
-    d.work = reinterpret_cast<double*>(b + h.off_work);
-    d.UW = b + h.off_UW;
+    d.scratch = b + h.off_scratch;
     d.meas = reinterpret_cast<double*>(b + h.off_meas);
+    d.last = reinterpret_cast<double*>(b + ctx->off_last) + (size_t)c * kRecord;
     d.max_meas = o.max_meas;
     d.dG = reinterpret_cast<double*>(b + h.off_dG);
     d.acc_log = reinterpret_cast<uint8_t*>(b + h.off_acc);
@@ -329,7 +344,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
-  e = launch_init(ctx->prec, ctx->d_desc, 0, n, o.seed, ctx->d_err, ctx->stream);
+  e = launch_init(ctx->prec, ctx->tpb, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "init launch"); }
   pqmc_status st = sync_check(ctx);
@@ -406,8 +421,8 @@ pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
   if (!ctx || n_sweeps < 0) return PQMC_EINVAL;
   if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
   if (n_sweeps == 0) return PQMC_OK;
-  cudaError_t e = launch_sweep(ctx->prec, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed, ctx->sweep_index,
-                               n_sweeps, measure, ctx->d_err, ctx->stream);
+  cudaError_t e = launch_sweep(ctx->prec, ctx->tpb, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed, ctx->sweep_index,
+                               n_sweeps, measure, ctx->res_bytes, ctx->d_err, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
   ctx->sweep_index += (uint32_t)n_sweeps;
@@ -493,6 +508,15 @@ pqmc_status pqmc_get_measurements(pqmc_ctx* ctx, int chain, double* out, long* n
   return PQMC_OK;
 }
 
+pqmc_status pqmc_get_last_records(pqmc_ctx* ctx, double* out) {
+  if (!ctx || !out) return PQMC_EINVAL;
+  pqmc_status s = sync_check(ctx);
+  if (s != PQMC_OK) return s;
+  cudaError_t e = cudaMemcpy(out, ctx->d_arena + ctx->off_last, ctx->chains.size() * kRecord * 8,
+                             cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "record copy");
+}
+
 pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields) {
   if (!chain_ok(ctx, chain) || !fields) return PQMC_EINVAL;
   if (ctx->sweep_index & 1u) return fail(ctx, PQMC_EINVAL, "set_fields needs an even number of sweeps done");
@@ -505,7 +529,7 @@ pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
-  e = launch_init(ctx->prec, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->d_err, ctx->stream);
+  e = launch_init(ctx->prec, ctx->tpb, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "init launch");
   return sync_check(ctx);
@@ -579,6 +603,17 @@ pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n)
   return PQMC_OK;
 }
 
+pqmc_status pqmc_get_phase_cycles(pqmc_ctx* ctx, int chain, long long* out) {
+  if (!chain_ok(ctx, chain) || !out) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  ChainState st;
+  pqmc_status s = read_state(ctx, chain, st);
+  if (s != PQMC_OK) return s;
+  for (int p = 0; p < kPhases; ++p) out[p] = st.cycles[p];
+  return PQMC_OK;
+}
+
 pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out) {
   if (!chain_ok(ctx, chain) || !out) return PQMC_EINVAL;
   const HostChain& h = ctx->chains[chain];
@@ -589,6 +624,8 @@ pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out) {
 int pqmc_num_chains(const pqmc_ctx* ctx) { return ctx ? (int)ctx->chains.size() : -1; }
 
 long pqmc_launch_count(const pqmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+size_t pqmc_device_bytes(const pqmc_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
 
 const char* pqmc_last_error(const pqmc_ctx* ctx) {
   if (!ctx) return g_init_error.c_str();

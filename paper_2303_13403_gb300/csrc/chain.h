@@ -6,9 +6,15 @@
 namespace pqmc {
 
 constexpr int kBlock = 32;        // sites per delayed-update block (one warp)
+constexpr int kMaxN = 1024;       // sites per chain
+constexpr int kMaxSigma = 512;    // particles per spin
+constexpr int kQRParts = 8;       // row chunks of the column dots in the Householder QR
 constexpr int kThreads = 256;     // threads per chain CTA
 constexpr int kRecord = 5;        // doubles per measurement record
 constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
+
+// phases timed with clock64() by thread 0 of each chain CTA
+enum : int { kPhFlip = 0, kPhFlush, kPhWrap, kPhStack, kPhQR, kPhRefresh, kPhMeasure, kPhTotal, kPhases };
 
 // error bits written by the kernels
 enum : int { kErrNaN = 1, kErrStab = 2, kErrTimeout = 4 };
@@ -24,6 +30,7 @@ struct ChainState {
   double max_dG;
   double logw[2][2];      // [spin][logabs, sign] at the last stabilisation
   double sign_stack;      // prod over spins of the weight sign at the last stabilisation
+  long long cycles[kPhases];  // SM clock cycles spent per phase (thread 0's view)
   int err;
   int pad;
 };
@@ -41,7 +48,6 @@ struct ChainDesc {
   double vexp[2][2][2];    // same indexing: e^{sigma kappa s}
   int8_t* fields;          // (Ltau+2) x N
   void* G;                 // 2 x N x ld (T)
-  void* Gt;                // 2 x N x ld (T), temporary
   const void* expKm;       // N x ld (T): e^{-dtau K}
   const void* expKp;       // N x ld (T): e^{+dtau K}
   const double* expKm64;   // N x N FP64
@@ -51,9 +57,10 @@ struct ChainDesc {
   double* Lst;             // (nb+1) x 2 x (N x nmax) FP64
   double* Rlog;            // (nb+1) x 2 x 2 (logabs, sign)
   double* Llog;            // (nb+1) x 2 x 2
-  double* work;            // FP64 scratch: M, Q (N x nmax each), O (nmax^2), Y (nmax x N)
-  void* UW;                // T scratch: 2 x (N x kBlock) + 2 x (kBlock x ld)
+  void* scratch;           // per-chain phase scratch in global memory (layout: ScratchLayout),
+                           // used when the chain does not fit in shared memory
   double* meas;            // max_meas x kRecord
+  double* last;            // kRecord: latest record (slot in a context-wide array)
   int max_meas;
   int pad0;
   double* dG;              // kDGHistory
@@ -61,5 +68,65 @@ struct ChainDesc {
   long long acc_cap;
   ChainState* st;
 };
+
+}  // namespace pqmc
+
+namespace pqmc {
+
+#if defined(__CUDACC__)
+#define PQMC_HDI __host__ __device__ inline
+#else
+#define PQMC_HDI inline
+#endif
+
+// Byte offsets of the phase buffers inside one chain's scratch region.  The
+// phases never overlap in time, so their buffers share the region:
+//   wrap    : Gt (N x ld, T) for one spin at a time
+//   flush   : U (kBlock x N, T) and W (kBlock x ld, T) for one spin
+//   stack   : M64 (N x n, FP64, column-major), then a region holding the two
+//             path-precision product buffers Mt, Mt2 (N x n, T, row-major)
+//             and later the FP64 Q of the QR; Householder betas / R_jj
+//   refresh : O, X (n x n, FP64, both spins), Y (n x ld, T), Q_R and Q_L in the
+//             path precision (N x n, T); LU pivots / multipliers
+struct ScratchLayout {
+  size_t gt, u, w, m64, mtq, mt2, qaux, o, x, y, qrt, qlt, laux, total;
+};
+
+PQMC_HDI size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
+  ScratchLayout L;
+  const size_t Nn = (size_t)N * n;
+  L.gt = 0;
+  size_t wrap = al16((size_t)N * ld * tsize);
+  L.u = 0;
+  L.w = al16((size_t)N * kBlock * tsize);
+  size_t flush = L.w + al16((size_t)kBlock * ld * tsize);
+  L.m64 = 0;
+  L.mtq = al16(Nn * 8);
+  L.mt2 = L.mtq + al16(Nn * tsize);
+  const size_t two_mt = 2 * al16(Nn * tsize);
+  const size_t mtq_sz = two_mt > al16(Nn * 8) ? two_mt : al16(Nn * 8);
+  L.qaux = L.mtq + mtq_sz;
+  size_t stack = L.qaux + al16((3 * (size_t)n + (size_t)kQRParts * n) * 8);
+  L.o = 0;                                   // O for spin 0, then spin 1
+  L.x = 2 * al16((size_t)n * n * 8);         // X for spin 0, then spin 1
+  L.y = L.x + 2 * al16((size_t)n * n * 8);
+  L.qrt = L.y + al16((size_t)n * ld * tsize);
+  L.qlt = L.qrt + al16(Nn * tsize);
+  L.laux = L.qlt + al16(Nn * tsize);
+  size_t refresh = L.laux + al16(2 * 3 * (size_t)n * 8);
+  size_t t = wrap;
+  if (flush > t) t = flush;
+  if (stack > t) t = stack;
+  if (refresh > t) t = refresh;
+  L.total = (t + 255) & ~(size_t)255;
+  return L;
+}
+
+// Shared-memory bytes of a chain that keeps G and its scratch resident.
+PQMC_HDI size_t resident_bytes(int N, int ld, int n, int tsize) {
+  return al16(2 * (size_t)N * ld * tsize) + scratch_layout(N, ld, n, tsize).total;
+}
 
 }  // namespace pqmc

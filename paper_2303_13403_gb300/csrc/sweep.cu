@@ -2,9 +2,9 @@
 //
 // One CTA owns one Markov chain for the whole launch and runs complete
 // sweeps: Metropolis flips of the Ising fields with delayed (blocked)
-// updates, slice wrapping, QR stabilisation of the B_L / B_R stacks in FP64,
-// and the measurement at the middle slice.  Chains are independent, so a
-// batch of chains of uneven size is one launch with one CTA per chain.
+// updates, slice wrapping, QR stabilisation of the B_L / B_R stacks, and the
+// measurement at the middle slice.  Chains are independent, so a batch of
+// chains of uneven size is one launch with one CTA per chain.
 //
 // Paper: Method section (PQMC estimator, Eq. (1) HS of the Gutzwiller
 // factor) and honeycomb Hubbard section (Eq. (2), trial state of Eq. (3)).
@@ -15,13 +15,22 @@
 //   G(tau) = 1 - B_R(tau) (B_L(tau) B_R(tau))^{-1} B_L(tau),
 //   B_R(tau) = B_tau ... B_0 P,  B_L(tau) = P^T B_{Ltau+1} ... B_{tau+1}.
 //   A flip of s_{tau,i} is proposed on G(tau-1): R_sigma = 1 + Delta_sigma (1 - G_ii).
+//
+// Precision: T (double or float) is the path precision of G, the ratios,
+// the wrap, the delayed updates, the products that advance the stack blocks
+// and the assembly of G from them.  The Householder QR of the stack blocks,
+// the product Q_L^T Q_R, its inverse and the log-determinant / sign are FP64
+// in every path.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "chain.h"
 #include "philox.cuh"
 
 namespace pqmc {
+
 
 // --------------------------------------------------------------------------
 // small CTA helpers
@@ -37,7 +46,13 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Sum over the CTA; every thread gets the result.  red holds >= 32 doubles.
+// Loop over a 2D index range with warps along rows and lanes along columns
+// (no runtime integer division in the element loops).
+#define PQMC_FOR_2D(i, i0, i1, j, j0, j1)                                          \
+  for (int i = (i0) + (int)(threadIdx.x >> 5); i < (i1); i += (int)(blockDim.x >> 5)) \
+    for (int j = (j0) + (int)(threadIdx.x & 31); j < (j1); j += 32)
+
+// Sum / max over the CTA; every thread gets the result.  red holds >= 32 doubles.
 __device__ double cta_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_sum(v);
@@ -45,8 +60,7 @@ __device__ double cta_sum(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double t = lane < nw ? red[lane] : 0.0;
-  t = warp_sum(t);
-  return t;
+  return warp_sum(t);
 }
 __device__ double cta_max(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -55,30 +69,59 @@ __device__ double cta_max(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double t = lane < nw ? red[lane] : 0.0;
-  t = warp_max(t);
-  return t;
+  return warp_max(t);
 }
 
 // --------------------------------------------------------------------------
-// CTA-wide register-tiled GEMM: C = A B with arbitrary strides,
-// A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj]; the epilogue receives
-// (i, j, value).  Every thread owns 4x4 outputs.
+// CTA-wide register-tiled GEMM: C = A B, A(i,k) = A[i*sai + k*sak],
+// B(k,j) = B[k*sbk + j*sbj]; inputs are converted to the accumulation type T
+// on load; the epilogue receives (i, j, value).  Every thread owns 4x4
+// outputs.  When A is contiguous in i and B in j (sai = sbj = 1, strides and
+// pointers 16-byte aligned, same type as T) the operands are read with
+// 16-byte vector loads.
 
 struct EpiStore {
-  template <typename T> __device__ void operator()(T* C, int sci, int scj, int i, int j, T v) const {
-    C[(long)i * sci + (long)j * scj] = v;
+  template <typename T, typename TC> __device__ void operator()(TC* C, int sci, int scj, int i, int j, T v) const {
+    C[(long)i * sci + (long)j * scj] = (TC)v;
   }
 };
 struct EpiSub {
-  template <typename T> __device__ void operator()(T* C, int sci, int scj, int i, int j, T v) const {
-    C[(long)i * sci + (long)j * scj] -= v;
+  template <typename T, typename TC> __device__ void operator()(TC* C, int sci, int scj, int i, int j, T v) const {
+    C[(long)i * sci + (long)j * scj] -= (TC)v;
   }
 };
 
-template <typename T, typename Epi>
-__device__ void cta_gemm(int M, int Nn, int K, const T* A, int sai, int sak, const T* B, int sbk,
-                         int sbj, T* C, int sci, int scj, Epi epi) {
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  __device__ static void load(const float* p, float v[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  static constexpr int kAlign = 4;
+};
+template <> struct Vec4<double> {
+  __device__ static void load(const double* p, double v[4]) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    const double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+  static constexpr int kAlign = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ bool vec_ok(const T* p, long stride) {
+  return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && (stride % Vec4<T>::kAlign == 0);
+}
+
+template <typename T, typename TA, typename TB, typename TC, typename Epi>
+__device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, const TB* B, int sbk, int sbj,
+                         TC* C, int sci, int scj, Epi epi) {
   const int tm = (M + 3) >> 2, tn = (Nn + 3) >> 2;
+  bool vec = false;
+  if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
+    vec = sai == 1 && sbj == 1 && vec_ok<T>((const T*)A, sak) && vec_ok<T>((const T*)B, sbk) &&
+          (M % 4 == 0) && (Nn % 4 == 0);
+  }
   for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
     const int i0 = (t / tn) << 2, j0 = (t % tn) << 2;
     T acc[4][4];
@@ -86,16 +129,34 @@ __device__ void cta_gemm(int M, int Nn, int K, const T* A, int sai, int sak, con
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
-    for (int k = 0; k < K; ++k) {
-      T a[4], b[4];
+    if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
+      if (vec) {
+        const T* pa = (const T*)A + i0;
+        const T* pb = (const T*)B + j0;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+          T a[4], b[4];
+          Vec4<T>::load(pa + (long)k * sak, a);
+          Vec4<T>::load(pb + (long)k * sbk, b);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = (i0 + r < M) ? A[(long)(i0 + r) * sai + (long)k * sak] : T(0);
+          for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = (j0 + q < Nn) ? B[(long)k * sbk + (long)(j0 + q) * sbj] : T(0);
+            for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+        }
+      }
+    }
+    if (!vec) {
+      for (int k = 0; k < K; ++k) {
+        T a[4], b[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r) a[r] = (i0 + r < M) ? (T)A[(long)(i0 + r) * sai + (long)k * sak] : T(0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+        for (int q = 0; q < 4; ++q) b[q] = (j0 + q < Nn) ? (T)B[(long)k * sbk + (long)(j0 + q) * sbj] : T(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+      }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -111,19 +172,23 @@ __device__ void cta_gemm(int M, int Nn, int K, const T* A, int sai, int sak, con
 template <typename T>
 struct Smem {
   T Gb[2][kBlock][kBlock + 1];      // diagonal block of current G, both spins
-  T xs[2][kBlock][kBlock];          // column snapshot at each accepted flip
-  T ys[2][kBlock][kBlock];          // row snapshot at each accepted flip
-  T Tu[2][kBlock][kBlock + 1];      // U = (E_S - G_{:,S}) Tu
-  T Tv[2][kBlock][kBlock + 1];      // W = Tv^T G_{S,:}
-  T cl[2][kBlock];                  // Delta / R_sigma of each accepted flip
+  T Tu[2][kBlock][kBlock + 1];      // 1 + (1 - G_SS) Gamma, inverted in place, then M
+  T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
   double u[kBlock];                 // Metropolis uniforms of the block
+  float uf[kBlock];                 // the same rounded down to 24 bits (FP32 decisions)
   double red[32];                   // reduction scratch
-  double qbeta[1024];               // Householder betas (n_sigma <= 1024)
-  double lmul[1024];                // LU multipliers
+  double vtab[2][2][2];             // e^{sigma kappa s}: [Gutzwiller?][spin][s = -1?]
+  T vt[2][2][2];                    // the same in the path precision
+  T vti[2][2][2];                   // and its inverse
+  long long cyc[kPhases];           // per-phase clock cycles (thread 0)
+  long long t_mark;
+  signed char fr[kMaxN];            // fields of the staged slice
   int sites[kBlock];                // block index of each accepted flip
   int fl[kBlock];                   // fields of the block
   int na;                           // accepted flips in the block
   int piv;
+  int nswap[2];
+  int staged;                       // slice held in fr, or -1
   double sign_running;
   double sign_spin[2];
   double logw_spin[2];
@@ -132,36 +197,87 @@ struct Smem {
   int err;
 };
 
+// One chain CTA: its descriptor, shared memory, and where G and the phase
+// scratch live (shared memory when they fit, else the chain's global buffers).
 template <typename T>
 struct Cta {
   const ChainDesc& c;
   Smem<T>& sh;
   uint64_t seed;
-  __device__ T* G(int s) const { return reinterpret_cast<T*>(c.G) + (long)s * c.N * c.ld; }
-  __device__ T* Gt(int s) const { return reinterpret_cast<T*>(c.Gt) + (long)s * c.N * c.ld; }
+  T* Gp;
+  unsigned char* scr;
+  ScratchLayout L;
+  bool resident;
+  __device__ T* G(int s) const { return Gp + (long)s * c.N * c.ld; }
+  __device__ T* Gt() const { return reinterpret_cast<T*>(scr + L.gt); }
+  __device__ T* Ub() const { return reinterpret_cast<T*>(scr + L.u); }
+  __device__ T* Wb() const { return reinterpret_cast<T*>(scr + L.w); }
+  __device__ double* M64() const { return reinterpret_cast<double*>(scr + L.m64); }
+  __device__ double* Q64() const { return reinterpret_cast<double*>(scr + L.mtq); }
+  __device__ T* Mt() const { return reinterpret_cast<T*>(scr + L.mtq); }
+  __device__ T* Mt2() const { return reinterpret_cast<T*>(scr + L.mt2); }
+  __device__ double* qbeta() const { return reinterpret_cast<double*>(scr + L.qaux); }
+  __device__ double* qalpha() const { return qbeta() + c.nmax; }
+  __device__ double* qw() const { return qbeta() + 2 * c.nmax; }
+  __device__ double* qpart() const { return qbeta() + 3 * c.nmax; }
+  __device__ double* Ob(int s) const {
+    return reinterpret_cast<double*>(scr + L.o + s * al16((size_t)c.nmax * c.nmax * 8));
+  }
+  __device__ double* Xb(int s) const {
+    return reinterpret_cast<double*>(scr + L.x + s * al16((size_t)c.nmax * c.nmax * 8));
+  }
+  __device__ T* Yb() const { return reinterpret_cast<T*>(scr + L.y); }
+  __device__ T* QRt() const { return reinterpret_cast<T*>(scr + L.qrt); }
+  __device__ T* QLt() const { return reinterpret_cast<T*>(scr + L.qlt); }
+  __device__ double* pval(int s) const { return reinterpret_cast<double*>(scr + L.laux) + s * 3 * c.nmax; }
+  __device__ double* pinv(int s) const { return pval(s) + c.nmax; }
+  __device__ double* lmul(int s) const { return pval(s) + 2 * c.nmax; }
   __device__ const T* Em() const { return reinterpret_cast<const T*>(c.expKm); }
   __device__ const T* Ep() const { return reinterpret_cast<const T*>(c.expKp); }
   __device__ int nsig(int s) const { return s == 0 ? c.nup : c.ndn; }
   __device__ bool gutz(int tau) const { return tau == 0 || tau == c.Ltau + 1; }
+  // stage the fields of slice tau into shared memory (collective)
+  __device__ void stage(int tau) {
+    __syncthreads();
+    const int8_t* f = c.fields + (long)tau * c.N;
+    for (int i = threadIdx.x; i < c.N; i += blockDim.x) sh.fr[i] = f[i];
+    if (threadIdx.x == 0) sh.staged = tau;
+    __syncthreads();
+  }
+  // diagonal of e^{V_sigma(s_tau)} at site i for the staged slice tau
   __device__ double vexp(int tau, int s, int i) const {
-    const int f = c.fields[(long)tau * c.N + i];
-    return c.vexp[gutz(tau) ? 1 : 0][s][f > 0 ? 0 : 1];
+    return sh.vtab[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
+  }
+  __device__ T vexpT(int tau, int s, int i) const { return sh.vt[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1]; }
+  __device__ T vinvT(int tau, int s, int i) const { return sh.vti[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1]; }
+  // charge the cycles since the last mark to phase ph (thread 0 only)
+  __device__ void mark(int ph) {
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      sh.cyc[ph] += t - sh.t_mark;
+      sh.t_mark = t;
+    }
   }
 };
 
 // --------------------------------------------------------------------------
 // Metropolis updates of one slice with delayed updates in blocks of kBlock
-// sites.  Inside a block one warp proposes the flips sequentially on the
-// kBlock x kBlock diagonal block of G (rank-1 updates restricted to the block)
-// and records, for the accepted set S, upper-triangular Tu and Tv such that
-// the sequence of Sherman-Morrison updates equals
-//     G <- G - (E_S - G_{:,S}) Tu Tv^T G_{S,:}
-// with G the G at the start of the block.  Column a of Tu / Tv follows from
-// the rank-1 form u_a = c_a (e_{s_a} - G^{(a)}_{:,s_a}),
-// v_a = G^{(a)}_{s_a,:}, G^{(a)} = G - sum_{l<a} u_l v_l^T:
-//     Tu[:,a] = c_a (e_a + sum_{l<a} Tu[:,l] v_l(s_a)),
-//     Tv[:,a] = e_a - sum_{l<a} Tv[:,l] u_l(s_a).
-// The whole CTA then applies the rank-|S| update to G.
+// sites.  Inside a block one warp (lane = column of the block) proposes the
+// flips in order on the kBlock x kBlock diagonal block of G.  Later proposals
+// read only rows and columns of later sites, so an accepted flip at j updates
+// just that future part: G_rq += c G_rj G_jq (r, q > j), c = Delta/R_sigma.
+// After the block the whole CTA applies the accepted set S at once:
+//     G <- G - (E_S - G_{:,S}) M G_{S,:},  M = Gamma (1 + (1 - G_SS) Gamma)^{-1},
+// G the G of the block start, Gamma = diag(Delta) of the accepted flips.  This
+// equals the sequence of Sherman-Morrison updates because the new G depends
+// only on the new fields; the pivots of the a x a inverse are the accepted
+// ratios, so Gauss-Jordan without pivoting follows the sequential process.
+
+template <typename T>
+__device__ __forceinline__ bool metropolis_accept(double u, float uf, T R) {
+  if constexpr (std::is_same<T, double>::value) return u < fabs(R);
+  else return uf < fabsf(R);
+}
 
 template <typename T>
 __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
@@ -171,8 +287,9 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int kap = x.gutz(tau) ? 1 : 0;
   int8_t* f = c.fields + (long)tau * N;
-  T* Ubuf = reinterpret_cast<T*>(c.UW);                // 2 x N x kBlock
-  T* Wbuf = Ubuf + 2L * N * kBlock;                    // 2 x kBlock x ld
+  T* Ubuf = x.Ub();                                    // kBlock x N  (U column-major, ld N)
+  T* Wbuf = x.Wb();                                    // kBlock x ld (rows G_{S,:})
+  const T dl[2][2] = {{(T)c.delta[kap][0][0], (T)c.delta[kap][0][1]}, {(T)c.delta[kap][1][0], (T)c.delta[kap][1][1]}};
 
   for (int i0 = 0; i0 < N; i0 += kBlock) {
     const int nbk = min(kBlock, N - i0);
@@ -182,7 +299,16 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
     }
     if (threadIdx.x < kBlock) {
       const int j = threadIdx.x;
-      sh.u[j] = j < nbk ? metropolis_uniform(x.seed, c.chain_index, sweep, (uint32_t)tau, (uint32_t)(i0 + j)) : 2.0;
+      if (j < nbk) {
+        const U4 w = philox4x32_10((uint32_t)(i0 + j), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
+                                   (uint32_t)(x.seed >> 32));
+        const uint64_t m53 = ((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11);
+        sh.u[j] = (double)m53 * 0x1.0p-53;
+        sh.uf[j] = (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;   // the same uniform rounded down to 24 bits
+      } else {
+        sh.u[j] = 2.0;
+        sh.uf[j] = 2.0f;
+      }
       sh.fl[j] = j < nbk ? (int)f[i0 + j] : 1;
     }
     __syncthreads();
@@ -191,47 +317,31 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
       int a = 0;
       for (int j = 0; j < nbk; ++j) {
         const int si = sh.fl[j] > 0 ? 0 : 1;
-        const T d0 = (T)c.delta[kap][0][si], d1 = (T)c.delta[kap][1][si];
+        const T d0 = dl[0][si], d1 = dl[1][si];
         const T r0 = T(1) + d0 * (T(1) - sh.Gb[0][j][j]);
         const T r1 = T(1) + d1 * (T(1) - sh.Gb[1][j][j]);
         const T R = r0 * r1;
-        const bool acc = sh.u[j] < fabs((double)R);
+        const bool acc = metropolis_accept<T>(sh.u[j], sh.uf[j], R);
         if (lane == 0) {
-          if (!isfinite((double)R)) sh.err |= kErrNaN;
+          if (!isfinite(R)) sh.err |= kErrNaN;
           if (sh.acc_pos < c.acc_cap) c.acc_log[sh.acc_pos] = acc ? 1 : 0;
           sh.acc_pos++;
           sh.n_prop++;
         }
         if (!acc) continue;
-        const T cc[2] = {d0 / r0, d1 / r1};
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          sh.xs[s][a][lane] = sh.Gb[s][lane][j];
-          sh.ys[s][a][lane] = sh.Gb[s][j][lane];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          T tu = (lane == a) ? T(1) : T(0);
-          T tv = tu;
-          if (lane < a) {
-            for (int l = lane; l < a; ++l) {
-              tu = fma(sh.Tu[s][lane][l], sh.ys[s][l][j], tu);
-              tv = fma(sh.Tv[s][lane][l], sh.cl[s][l] * sh.xs[s][l][j], tv);
-            }
-          }
-          sh.Tu[s][lane][a] = lane <= a ? cc[s] * tu : T(0);
-          sh.Tv[s][lane][a] = lane <= a ? tv : T(0);
-          const T yq = sh.ys[s][a][lane];
-          for (int r = 0; r < nbk; ++r) {
-            const T xr = sh.xs[s][a][r];
-            sh.Gb[s][r][lane] -= cc[s] * ((r == j ? T(1) : T(0)) - xr) * yq;
+        const T c0 = d0 / r0, c1 = d1 / r1;
+        if (lane > j && lane < nbk) {
+          const T y0 = c0 * sh.Gb[0][j][lane], y1 = c1 * sh.Gb[1][j][lane];
+#pragma unroll 4
+          for (int r = j + 1; r < nbk; ++r) {
+            sh.Gb[0][r][lane] = fma(sh.Gb[0][r][j], y0, sh.Gb[0][r][lane]);
+            sh.Gb[1][r][lane] = fma(sh.Gb[1][r][j], y1, sh.Gb[1][r][lane]);
           }
         }
         if (lane == 0) {
           sh.sites[a] = j;
-          sh.cl[0][a] = cc[0];
-          sh.cl[1][a] = cc[1];
+          sh.cl[0][a] = d0;
+          sh.cl[1][a] = d1;
           sh.fl[j] = -sh.fl[j];
           f[i0 + j] = (int8_t)sh.fl[j];
           sh.sign_running *= (R < T(0)) ? -1.0 : 1.0;
@@ -243,33 +353,56 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
       if (lane == 0) sh.na = a;
     }
     __syncthreads();
+    x.mark(kPhFlip);
     const int a = sh.na;
     if (a == 0) continue;
 
-    // U[i][l'] = sum_{l<=l'} (delta_{i, s_l} - G[i][s_l]) Tu[l][l']   (N x a)
-    // W[l'][q] = sum_{l<=l'} Tv[l][l'] G[s_l][q]                      (a x N)
-    for (int e = threadIdx.x; e < 2 * N * a; e += blockDim.x) {
-      const int s = e / (N * a), rem = e % (N * a), i = rem / a, lp = rem % a;
-      const T* Gs = x.G(s);
-      T acc = T(0);
-      for (int l = 0; l <= lp; ++l) {
-        const int col = i0 + sh.sites[l];
-        acc = fma((i == col ? T(1) : T(0)) - Gs[(long)i * ld + col], sh.Tu[s][l][lp], acc);
+    // X = 1 + (1 - G_SS) Gamma (block-start G), inverted in place by one warp
+    // per spin; then M = Gamma X^{-1} (stored in Tu)
+    PQMC_FOR_2D(sl, 0, 2 * a, m, 0, a) {
+      const int s = sl >= a ? 1 : 0, l = sl - s * a;
+      const T g = x.G(s)[(long)(i0 + sh.sites[l]) * ld + i0 + sh.sites[m]];
+      sh.Tu[s][l][m] = ((l == m) ? T(1) : T(0)) + ((l == m ? T(1) : T(0)) - g) * sh.cl[s][m];
+    }
+    __syncthreads();
+    if (warp < 2) {
+      const int s = warp;
+      T (*X)[kBlock + 1] = sh.Tu[s];
+      for (int p = 0; p < a; ++p) {
+        const T ip = T(1) / X[p][p];
+        const T xpl = lane < a ? X[p][lane] : T(0);
+        if (lane < a && lane != p)
+          for (int r = 0; r < a; ++r)
+            if (r != p) X[r][lane] = fma(-X[r][p] * ip, xpl, X[r][lane]);
+        __syncwarp();
+        if (lane < a) {
+          if (lane != p) X[p][lane] = xpl * ip;
+          X[lane][p] = lane == p ? ip : -X[lane][p] * ip;
+        }
+        __syncwarp();
       }
-      Ubuf[(long)s * N * kBlock + (long)i * kBlock + lp] = acc;
-    }
-    for (int e = threadIdx.x; e < 2 * N * a; e += blockDim.x) {
-      const int s = e / (N * a), rem = e % (N * a), lp = rem / N, q = rem % N;
-      const T* Gs = x.G(s);
-      T acc = T(0);
-      for (int l = 0; l <= lp; ++l) acc = fma(sh.Tv[s][l][lp], Gs[(long)(i0 + sh.sites[l]) * ld + q], acc);
-      Wbuf[(long)s * kBlock * ld + (long)lp * ld + q] = acc;
+      for (int l = 0; l < a; ++l)
+        if (lane < a) X[l][lane] *= sh.cl[s][l];
     }
     __syncthreads();
-    for (int s = 0; s < 2; ++s)
-      cta_gemm<T>(N, N, a, Ubuf + (long)s * N * kBlock, kBlock, 1, Wbuf + (long)s * kBlock * ld, ld, 1,
-                  x.G(s), ld, 1, EpiSub());
-    __syncthreads();
+    // per spin: U[:, m] = sum_l (e_{s_l} - G[:, s_l]) M[l][m]  (N x a, column-major),
+    // W = G_{S,:} (a x N) read before G changes, then G -= U W
+    for (int s = 0; s < 2; ++s) {
+      T* Gs = x.G(s);
+      PQMC_FOR_2D(m, 0, a, i, 0, N) {
+        T acc = T(0);
+        for (int l = 0; l < a; ++l) {
+          const int col = i0 + sh.sites[l];
+          acc = fma((i == col ? T(1) : T(0)) - Gs[(long)i * ld + col], sh.Tu[s][l][m], acc);
+        }
+        Ubuf[(long)m * N + i] = acc;
+      }
+      PQMC_FOR_2D(l, 0, a, q, 0, N) Wbuf[(long)l * ld + q] = Gs[(long)(i0 + sh.sites[l]) * ld + q];
+      __syncthreads();
+      cta_gemm<T>(N, N, a, Ubuf, 1, N, Wbuf, ld, 1, Gs, ld, 1, EpiSub());
+      __syncthreads();
+    }
+    x.mark(kPhFlush);
   }
 }
 
@@ -282,32 +415,34 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
   const ChainDesc& c = x.c;
   const int N = c.N, ld = c.ld;
   const bool gz = x.gutz(tau);
+  T* Gt = x.Gt();
+  x.stage(tau);
   if (dir > 0) {
-    for (int e = threadIdx.x; e < 2 * N * N; e += blockDim.x) {
-      const int s = e / (N * N), i = (e / N) % N, j = e % N;
-      x.G(s)[(long)i * ld + j] *= (T)(x.vexp(tau, s, i) / x.vexp(tau, s, j));
+    for (int s = 0; s < 2; ++s) {
+      T* Gs = x.G(s);
+      PQMC_FOR_2D(i, 0, N, j, 0, N) Gs[(long)i * ld + j] *= x.vexpT(tau, s, i) * x.vinvT(tau, s, j);
     }
     __syncthreads();
     if (gz) return;
     // Gt = e^{-dtau K} G (stored transposed), G = Gt e^{+dtau K}
-    for (int s = 0; s < 2; ++s)
-      cta_gemm<T>(N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, x.Gt(s), 1, ld, EpiStore());
-    __syncthreads();
-    for (int s = 0; s < 2; ++s)
-      cta_gemm<T>(N, N, N, x.Gt(s), 1, ld, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
-    __syncthreads();
-  } else {
-    if (!gz) {
-      for (int s = 0; s < 2; ++s)
-        cta_gemm<T>(N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, x.Gt(s), 1, ld, EpiStore());
+    for (int s = 0; s < 2; ++s) {
+      cta_gemm<T>(N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
       __syncthreads();
-      for (int s = 0; s < 2; ++s)
-        cta_gemm<T>(N, N, N, x.Gt(s), 1, ld, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
+      cta_gemm<T>(N, N, N, Gt, 1, ld, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < 2 * N * N; e += blockDim.x) {
-      const int s = e / (N * N), i = (e / N) % N, j = e % N;
-      x.G(s)[(long)i * ld + j] *= (T)(x.vexp(tau, s, j) / x.vexp(tau, s, i));
+  } else {
+    if (!gz) {
+      for (int s = 0; s < 2; ++s) {
+        cta_gemm<T>(N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
+        __syncthreads();
+        cta_gemm<T>(N, N, N, Gt, 1, ld, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
+        __syncthreads();
+      }
+    }
+    for (int s = 0; s < 2; ++s) {
+      T* Gs = x.G(s);
+      PQMC_FOR_2D(i, 0, N, j, 0, N) Gs[(long)i * ld + j] *= x.vexpT(tau, s, j) * x.vinvT(tau, s, i);
     }
     __syncthreads();
   }
@@ -316,79 +451,128 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
 // --------------------------------------------------------------------------
 // FP64 stabilisation.
 
-// Householder QR of the column-major N x n matrix M (ld N).  The explicit
-// orthonormal factor goes to Q (column-major, ld N); log|det R| and sign(det R)
-// are returned through the shared variables.
+// log|prod_j d_j| and sign(prod_j d_j) of n values in shared memory, summed by
+// warp 0 and broadcast through shared memory (collective).
 template <typename T>
-__device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs, double& sgn) {
-  Smem<T>& sh = x.sh;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ double s_alpha;
-  double la = 0.0, sg = 1.0;
-  for (int j = 0; j < n; ++j) {
-    double* v = M + (long)j * N;
-    if (warp == 0) {
-      double s = 0.0;
-      for (int i = j + lane; i < N; i += 32) s += v[i] * v[i];
-      s = warp_sum(s);
-      if (lane == 0) {
-        const double x0 = v[j];
-        const double alpha = x0 > 0 ? -sqrt(s) : sqrt(s);
-        const double v0 = x0 - alpha;
-        const double vv = s - x0 * x0 + v0 * v0;
-        v[j] = v0;
-        sh.qbeta[j] = vv > 0 ? 2.0 / vv : 0.0;
-        s_alpha = alpha;
-        if (alpha == 0.0) sh.err |= kErrStab;
-      }
-    }
-    __syncthreads();
-    la += log(fabs(s_alpha));
-    sg *= s_alpha < 0 ? -1.0 : 1.0;
-    const double beta = sh.qbeta[j];
-    for (int col = j + 1 + warp; col < n; col += nw) {
-      double* w = M + (long)col * N;
-      double d = 0.0;
-      for (int i = j + lane; i < N; i += 32) d += v[i] * w[i];
-      d = warp_sum(d) * beta;
-      for (int i = j + lane; i < N; i += 32) w[i] -= d * v[i];
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < N * n; e += blockDim.x) {
-    const int col = e / N, i = e % N;
-    Q[e] = (i == col) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int j = n - 1; j >= 0; --j) {
-    const double* v = M + (long)j * N;
-    const double beta = sh.qbeta[j];
-    for (int col = j + warp; col < n; col += nw) {
-      double* w = Q + (long)col * N;
-      double d = 0.0;
-      for (int i = j + lane; i < N; i += 32) d += v[i] * w[i];
-      d = warp_sum(d) * beta;
-      for (int i = j + lane; i < N; i += 32) w[i] -= d * v[i];
-    }
-    __syncthreads();
-  }
-  logabs = la;
-  sgn = sg;
-}
-
-// Solve O Y = Y in place by LU with partial pivoting (O: n x n row-major;
-// Y: n x ncols row-major, ld ncols).  Returns log|det O| and sign(det O).
-template <typename T>
-__device__ void lu_solve(Cta<T>& x, int n, int ncols, double* O, double* Y, double& logabs, double& sgn) {
+__device__ void log_det_of(Cta<T>& x, const double* d, int n, int extra_sign_flips, double& logabs, double& sgn) {
   Smem<T>& sh = x.sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double la = 0.0, sg = 1.0;
+  __syncthreads();
+  if (warp == 0) {
+    double la = 0.0;
+    int neg = 0;
+    for (int j = lane; j < n; j += 32) {
+      la += log(fabs(d[j]));
+      neg += d[j] < 0 ? 1 : 0;
+    }
+    la = warp_sum(la);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) neg += __shfl_xor_sync(0xffffffffu, neg, o);
+    if (lane == 0) {
+      sh.red[0] = la;
+      sh.red[1] = ((neg + extra_sign_flips) & 1) ? -1.0 : 1.0;
+    }
+  }
+  __syncthreads();
+  logabs = sh.red[0];
+  sgn = sh.red[1];
+  __syncthreads();
+}
+
+// Householder QR of the column-major N x n matrix M (ld N).  The explicit
+// orthonormal factor goes to Q (column-major, ld N); log|det R| and sign(det R)
+// are returned to every thread.  Each reflector is applied to all trailing
+// columns in three CTA-wide phases (partial column dots over row chunks, one
+// thread per column adds the chunks, a parallel rank-1 update), so no FP64
+// work sits in warp-shuffle reductions.
+template <typename T>
+__device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta, double* A, int c0, int c1, int j) {
+  double* part = x.qpart();
+  double* w = x.qw();
+  if (c1 <= c0) return;
+  // thread (col, p): rows j + p, j + p + kQRParts, ...
+  {
+    const int p = threadIdx.x & (kQRParts - 1);
+    for (int col = c0 + (int)(threadIdx.x / kQRParts); col < c1; col += (int)(blockDim.x / kQRParts)) {
+      const double* a = A + (long)col * N;
+      double d0 = 0.0, d1 = 0.0;
+      int i = j + p;
+      for (; i + kQRParts < N; i += 2 * kQRParts) {
+        d0 = fma(v[i], a[i], d0);
+        d1 = fma(v[i + kQRParts], a[i + kQRParts], d1);
+      }
+      if (i < N) d0 = fma(v[i], a[i], d0);
+      part[p * x.c.nmax + col] = d0 + d1;
+    }
+  }
+  __syncthreads();
+  for (int col = c0 + threadIdx.x; col < c1; col += blockDim.x) {
+    double d = 0.0;
+#pragma unroll
+    for (int p = 0; p < kQRParts; ++p) d += part[p * x.c.nmax + col];
+    w[col] = d * beta;
+  }
+  __syncthreads();
+  PQMC_FOR_2D(col, c0, c1, i, j, N) A[(long)col * N + i] = fma(-v[i], w[col], A[(long)col * N + i]);
+  __syncthreads();
+}
+
+// reflector of column j (warp 0): v = x - alpha e_j stored over the column
+template <typename T>
+__device__ void householder_reflector(Cta<T>& x, int N, double* M, int j) {
+  const int lane = threadIdx.x & 31;
+  if ((threadIdx.x >> 5) == 0) {
+    double* v = M + (long)j * N;
+    double s = 0.0;
+    for (int i = j + lane; i < N; i += 32) s = fma(v[i], v[i], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double x0 = v[j];
+      const double a = x0 > 0 ? -sqrt(s) : sqrt(s);
+      const double v0 = x0 - a;
+      const double vv = s - x0 * x0 + v0 * v0;
+      v[j] = v0;
+      x.qbeta()[j] = vv > 0 ? 2.0 / vv : 0.0;
+      x.qalpha()[j] = a;
+      if (a == 0.0) x.sh.err |= kErrStab;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs, double& sgn) {
   for (int j = 0; j < n; ++j) {
-    if (warp == 0) {
+    householder_reflector(x, N, M, j);
+    householder_apply(x, N, M + (long)j * N, x.qbeta()[j], M, j + 1, n, j);
+  }
+  PQMC_FOR_2D(col, 0, n, i, 0, N) Q[(long)col * N + i] = (i == col) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) householder_apply(x, N, M + (long)j * N, x.qbeta()[j], Q, j, n, j);
+  log_det_of(x, x.qalpha(), n, 0, logabs, sgn);
+}
+
+// Solve O_s Y_s = Y_s in place for both spins at once by LU with partial
+// pivoting (O_s: n_s x n_s row-major; Y_s: n_s x ncols_s row-major).  Warp 0
+// finds the pivots, swaps the rows and forms the multipliers; the CTA applies
+// the eliminations.  Returns log|det O_s| and sign(det O_s) to every thread.
+template <typename T>
+__device__ void lu_solve2(Cta<T>& x, const int n[2], const int ncols[2], double* O[2], double* Y[2],
+                          double logabs[2], double sgn[2]) {
+  Smem<T>& sh = x.sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nmax = n[0] > n[1] ? n[0] : n[1];
+  if (threadIdx.x < 2) sh.nswap[threadIdx.x] = 0;
+  __syncthreads();
+  for (int j = 0; j < nmax; ++j) {
+    if (warp < 2 && j < n[warp]) {
+      const int s = warp, ns = n[s], nc = ncols[s];
+      double* Os = O[s];
+      double* Ys = Y[s];
       double best = -1.0;
       int bi = j;
-      for (int i = j + lane; i < n; i += 32) {
-        const double v = fabs(O[(long)i * n + j]);
+      for (int i = j + lane; i < ns; i += 32) {
+        const double v = fabs(Os[(long)i * ns + j]);
         if (v > best) { best = v; bi = i; }
       }
 #pragma unroll
@@ -397,58 +581,69 @@ __device__ void lu_solve(Cta<T>& x, int n, int ncols, double* O, double* Y, doub
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) sh.piv = bi;
-    }
-    __syncthreads();
-    const int p = sh.piv;
-    if (p != j) {
-      for (int e = threadIdx.x; e < n + ncols; e += blockDim.x) {
-        double* A = e < n ? O : Y;
-        const int ldA = e < n ? n : ncols;
-        const int col = e < n ? e : e - n;
-        const double t = A[(long)j * ldA + col];
-        A[(long)j * ldA + col] = A[(long)p * ldA + col];
-        A[(long)p * ldA + col] = t;
+      if (bi != j) {
+        for (int col = lane; col < ns; col += 32) {
+          const double t = Os[(long)j * ns + col];
+          Os[(long)j * ns + col] = Os[(long)bi * ns + col];
+          Os[(long)bi * ns + col] = t;
+        }
+        for (int col = lane; col < nc; col += 32) {
+          const double t = Ys[(long)j * nc + col];
+          Ys[(long)j * nc + col] = Ys[(long)bi * nc + col];
+          Ys[(long)bi * nc + col] = t;
+        }
+        if (lane == 0) sh.nswap[s]++;
       }
-      sg = -sg;
-      __syncthreads();
-    }
-    const double piv = O[(long)j * n + j];
-    if (piv == 0.0) {
-      if (threadIdx.x == 0) sh.err |= kErrStab;
-      __syncthreads();
-      logabs = -INFINITY;
-      sgn = 0.0;
-      return;
-    }
-    la += log(fabs(piv));
-    sg *= piv < 0 ? -1.0 : 1.0;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) sh.lmul[i] = O[(long)i * n + j] / piv;
-    __syncthreads();
-    const int w = n - j - 1 + ncols;
-    const long total = (long)(n - j - 1) * w;
-    for (long e = threadIdx.x; e < total; e += blockDim.x) {
-      const int i = j + 1 + (int)(e / w), col = (int)(e % w);
-      if (col < n - j - 1)
-        O[(long)i * n + j + 1 + col] -= sh.lmul[i] * O[(long)j * n + j + 1 + col];
-      else
-        Y[(long)i * ncols + col - (n - j - 1)] -= sh.lmul[i] * Y[(long)j * ncols + col - (n - j - 1)];
+      __syncwarp();
+      const double pv = Os[(long)j * ns + j];
+      const double pinv = pv != 0.0 ? 1.0 / pv : 0.0;
+      if (lane == 0) {
+        x.pval(s)[j] = pv;
+        x.pinv(s)[j] = pinv;
+        if (pv == 0.0) sh.err |= kErrStab;
+      }
+      for (int i = j + 1 + lane; i < ns; i += 32) x.lmul(s)[i] = Os[(long)i * ns + j] * pinv;
     }
     __syncthreads();
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const double inv = 1.0 / O[(long)j * n + j];
-    for (int col = threadIdx.x; col < ncols; col += blockDim.x) Y[(long)j * ncols + col] *= inv;
-    __syncthreads();
-    const long total = (long)j * ncols;
-    for (long e = threadIdx.x; e < total; e += blockDim.x) {
-      const int i = (int)(e / ncols), col = (int)(e % ncols);
-      Y[(long)i * ncols + col] -= O[(long)i * n + j] * Y[(long)j * ncols + col];
+    for (int s = 0; s < 2; ++s) {
+      if (j >= n[s]) continue;
+      const int ns = n[s], nc = ncols[s];
+      double* Os = O[s];
+      double* Ys = Y[s];
+      const double* lm = x.lmul(s);
+      const int nt = ns - j - 1;
+      PQMC_FOR_2D(i, j + 1, ns, col, 0, nt + nc) {
+        if (col < nt)
+          Os[(long)i * ns + j + 1 + col] = fma(-lm[i], Os[(long)j * ns + j + 1 + col], Os[(long)i * ns + j + 1 + col]);
+        else
+          Ys[(long)i * nc + col - nt] = fma(-lm[i], Ys[(long)j * nc + col - nt], Ys[(long)i * nc + col - nt]);
+      }
     }
     __syncthreads();
   }
-  logabs = la;
-  sgn = sg;
+  // back substitution, both spins
+  for (int j = nmax - 1; j >= 0; --j) {
+    for (int s = 0; s < 2; ++s) {
+      if (j >= n[s]) continue;
+      const double inv = x.pinv(s)[j];
+      for (int col = threadIdx.x; col < ncols[s]; col += blockDim.x) Y[s][(long)j * ncols[s] + col] *= inv;
+    }
+    __syncthreads();
+    for (int s = 0; s < 2; ++s) {
+      if (j >= n[s]) continue;
+      const int ns = n[s], nc = ncols[s];
+      PQMC_FOR_2D(i, 0, j, col, 0, nc)
+        Y[s][(long)i * nc + col] = fma(-O[s][(long)i * ns + j], Y[s][(long)j * nc + col], Y[s][(long)i * nc + col]);
+    }
+    __syncthreads();
+  }
+  for (int s = 0; s < 2; ++s) log_det_of(x, x.pval(s), n[s], sh.nswap[s], logabs[s], sgn[s]);
+}
+
+__device__ void copy_block(const double* src, double* dst, int n) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+  __syncthreads();
 }
 
 template <typename T>
@@ -457,36 +652,43 @@ __device__ double* stack_block(const Cta<T>& x, double* base, int b, int s) {
 }
 
 // Right stack block b: QR of B_{b n} ... B_{(b-1)n+1} Q_R[b-1] (b >= 1) or of B_0 P (b = 0).
+// The slice products run in the path precision on a row-major copy.
 template <typename T>
 __device__ void push_R(Cta<T>& x, int b) {
   const ChainDesc& c = x.c;
   const int N = c.N, n_stab = c.n_stab;
-  double* M = c.work;
-  double* M2 = c.work + (long)N * c.nmax;
+  double* M = x.M64();
   for (int s = 0; s < 2; ++s) {
     const int n = x.nsig(s);
     const double* P = c.P + (long)s * N * c.nmax;
+    T* Mt = x.Mt();
+    T* Mt2 = x.Mt2();
     double prev_l = 0.0, prev_s = 1.0;
     if (b == 0) {
-      for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] = x.vexp(0, s, e % N) * P[e];
+      x.stage(0);
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = x.vexp(0, s, i) * P[(long)k * N + i];
       __syncthreads();
     } else {
       const double* prev = stack_block(x, c.Rst, b - 1, s);
-      for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] = prev[e];
+      PQMC_FOR_2D(k, 0, n, i, 0, N) Mt[(long)i * n + k] = (T)prev[(long)k * N + i];
       prev_l = c.Rlog[((b - 1) * 2 + s) * 2 + 0];
       prev_s = c.Rlog[((b - 1) * 2 + s) * 2 + 1];
-      __syncthreads();
       for (int tau = (b - 1) * n_stab + 1; tau <= b * n_stab; ++tau) {
-        for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] *= x.vexp(tau, s, e % N);
+        x.stage(tau);
+        PQMC_FOR_2D(i, 0, N, k, 0, n) Mt[(long)i * n + k] *= x.vexpT(tau, s, i);
         __syncthreads();
-        cta_gemm<double>(N, n, N, c.expKm64, 1, N, M, 1, N, M2, 1, N, EpiStore());
+        cta_gemm<T>(N, n, N, x.Em(), 1, c.ld, Mt, n, 1, Mt2, n, 1, EpiStore());
         __syncthreads();
-        for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] = M2[e];
-        __syncthreads();
+        T* t = Mt; Mt = Mt2; Mt2 = t;
       }
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
+      __syncthreads();
     }
     double la, sg;
-    qr_householder(x, N, n, M, stack_block(x, c.Rst, b, s), la, sg);
+    x.mark(kPhStack);
+    qr_householder(x, N, n, M, x.Q64(), la, sg);
+    copy_block(x.Q64(), stack_block(x, c.Rst, b, s), N * n);
+    x.mark(kPhQR);
     if (threadIdx.x == 0) {
       c.Rlog[(b * 2 + s) * 2 + 0] = prev_l + la;
       c.Rlog[(b * 2 + s) * 2 + 1] = prev_s * sg;
@@ -501,30 +703,37 @@ template <typename T>
 __device__ void push_L(Cta<T>& x, int b) {
   const ChainDesc& c = x.c;
   const int N = c.N, n_stab = c.n_stab;
-  double* M = c.work;
-  double* M2 = c.work + (long)N * c.nmax;
+  double* M = x.M64();
   for (int s = 0; s < 2; ++s) {
     const int n = x.nsig(s);
     const double* P = c.P + (long)s * N * c.nmax;
+    T* Mt = x.Mt();
+    T* Mt2 = x.Mt2();
     double prev_l = 0.0, prev_s = 1.0;
     if (b == c.nb) {
-      for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] = x.vexp(c.Ltau + 1, s, e % N) * P[e];
+      x.stage(c.Ltau + 1);
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = x.vexp(c.Ltau + 1, s, i) * P[(long)k * N + i];
       __syncthreads();
     } else {
       const double* prev = stack_block(x, c.Lst, b + 1, s);
-      for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] = prev[e];
+      PQMC_FOR_2D(k, 0, n, i, 0, N) Mt[(long)i * n + k] = (T)prev[(long)k * N + i];
       prev_l = c.Llog[((b + 1) * 2 + s) * 2 + 0];
       prev_s = c.Llog[((b + 1) * 2 + s) * 2 + 1];
       __syncthreads();
       for (int tau = (b + 1) * n_stab; tau > b * n_stab; --tau) {
-        cta_gemm<double>(N, n, N, c.expKm64, 1, N, M, 1, N, M2, 1, N, EpiStore());
-        __syncthreads();
-        for (int e = threadIdx.x; e < N * n; e += blockDim.x) M[e] = x.vexp(tau, s, e % N) * M2[e];
+        cta_gemm<T>(N, n, N, x.Em(), 1, c.ld, Mt, n, 1, Mt2, n, 1, EpiStore());
+        x.stage(tau);
+        PQMC_FOR_2D(i, 0, N, k, 0, n) Mt[(long)i * n + k] = x.vexpT(tau, s, i) * Mt2[(long)i * n + k];
         __syncthreads();
       }
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
+      __syncthreads();
     }
     double la, sg;
-    qr_householder(x, N, n, M, stack_block(x, c.Lst, b, s), la, sg);
+    x.mark(kPhStack);
+    qr_householder(x, N, n, M, x.Q64(), la, sg);
+    copy_block(x.Q64(), stack_block(x, c.Lst, b, s), N * n);
+    x.mark(kPhQR);
     if (threadIdx.x == 0) {
       c.Llog[(b * 2 + s) * 2 + 0] = prev_l + la;
       c.Llog[(b * 2 + s) * 2 + 1] = prev_s * sg;
@@ -533,6 +742,22 @@ __device__ void push_L(Cta<T>& x, int b) {
   }
 }
 
+// Fused epilogue of the G assembly: g = delta_ij - v, compare with the
+// propagated G, overwrite it.
+template <typename T>
+struct EpiFresh {
+  T* G;
+  int ld;
+  T* dmax;
+  template <typename A, typename TC> __device__ void operator()(TC*, int, int, int i, int j, A v) const {
+    const T g = (i == j ? T(1) : T(0)) - (T)v;
+    T& ref = G[(long)i * ld + j];
+    const T d = fabs(ref - g);
+    *dmax = d > *dmax ? d : *dmax;
+    ref = g;
+  }
+};
+
 // G <- 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T at stabilisation point b; records
 // max |G - G_fresh| when record != 0, and the weight's log|det| and sign.
 template <typename T>
@@ -540,51 +765,43 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
   const ChainDesc& c = x.c;
   Smem<T>& sh = x.sh;
   const int N = c.N, ld = c.ld;
-  double* O = c.work + 2L * N * c.nmax;
-  double* Y = O + (long)c.nmax * c.nmax;
-  double dmax = 0.0;
+  T* Y = x.Yb();
+  T dmax = T(0);
   double sign_total = 1.0;
+  int n[2] = {x.nsig(0), x.nsig(1)};
+  double* O[2] = {x.Ob(0), x.Ob(1)};
+  double* X[2] = {x.Xb(0), x.Xb(1)};
+  const double* QR[2] = {stack_block(x, c.Rst, b, 0), stack_block(x, c.Rst, b, 1)};
+  const double* QL[2] = {stack_block(x, c.Lst, b, 0), stack_block(x, c.Lst, b, 1)};
+  // O_s = Q_L^T Q_R and X_s = O_s^{-1} in FP64, both spins together
   for (int s = 0; s < 2; ++s) {
-    const int n = x.nsig(s);
-    const double* QR = stack_block(x, c.Rst, b, s);
-    const double* QL = stack_block(x, c.Lst, b, s);
-    cta_gemm<double>(n, n, N, QL, N, 1, QR, 1, N, O, n, 1, EpiStore());
-    for (int e = threadIdx.x; e < n * N; e += blockDim.x) Y[e] = QL[e];
-    __syncthreads();
-    double la, sg;
-    lu_solve(x, n, N, O, Y, la, sg);
-    // G_fresh = 1 - QR Y, compared with and written over G
-    T* Gs = x.G(s);
-    const int tm = (N + 3) >> 2;
-    for (int t = threadIdx.x; t < tm * tm; t += blockDim.x) {
-      const int i0 = (t / tm) << 2, j0 = (t % tm) << 2;
-      double acc[4][4] = {};
-      for (int k = 0; k < n; ++k) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) av[r] = (i0 + r < N) ? QR[(long)k * N + i0 + r] : 0.0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bv[q] = (j0 + q < N) ? Y[(long)k * N + j0 + q] : 0.0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+    cta_gemm<double>(n[s], n[s], N, QL[s], N, 1, QR[s], 1, N, O[s], n[s], 1, EpiStore());
+    PQMC_FOR_2D(r, 0, n[s], q, 0, n[s]) X[s][(long)r * n[s] + q] = (r == q) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  double la[2], sg[2];
+  lu_solve2(x, n, n, O, X, la, sg);
+  for (int s = 0; s < 2; ++s) {
+    // Y = X Q_L^T (n x N), G_fresh = 1 - Q_R Y, in the path precision
+    const T* qr = reinterpret_cast<const T*>(QR[s]);
+    const T* ql = reinterpret_cast<const T*>(QL[s]);
+    if constexpr (!std::is_same<T, double>::value) {
+      T* qrt = x.QRt();
+      T* qlt = x.QLt();
+      PQMC_FOR_2D(k, 0, n[s], i, 0, N) {
+        qrt[(long)k * N + i] = (T)QR[s][(long)k * N + i];
+        qlt[(long)k * N + i] = (T)QL[s][(long)k * N + i];
       }
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = i0 + r, j = j0 + q;
-          if (i < N && j < N) {
-            const double g = (i == j ? 1.0 : 0.0) - acc[r][q];
-            T& ref = Gs[(long)i * ld + j];
-            dmax = fmax(dmax, fabs((double)ref - g));
-            ref = (T)g;
-          }
-        }
+      qr = qrt;
+      ql = qlt;
+      __syncthreads();
     }
-    const double l_tot = c.Rlog[(b * 2 + s) * 2 + 0] + la + c.Llog[(b * 2 + s) * 2 + 0];
-    const double s_tot = c.Rlog[(b * 2 + s) * 2 + 1] * sg * c.Llog[(b * 2 + s) * 2 + 1];
+    cta_gemm<T>(n[s], N, n[s], X[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
+    __syncthreads();
+    EpiFresh<T> epi{x.G(s), ld, &dmax};
+    cta_gemm<T>(N, N, n[s], qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
+    const double l_tot = c.Rlog[(b * 2 + s) * 2 + 0] + la[s] + c.Llog[(b * 2 + s) * 2 + 0];
+    const double s_tot = c.Rlog[(b * 2 + s) * 2 + 1] * sg[s] * c.Llog[(b * 2 + s) * 2 + 1];
     if (threadIdx.x == 0) {
       sh.logw_spin[s] = l_tot;
       sh.sign_spin[s] = s_tot;
@@ -592,8 +809,9 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     sign_total *= s_tot;
     __syncthreads();
   }
-  dmax = cta_max(dmax, sh.red);
+  const double dm = cta_max((double)dmax, sh.red);
   if (threadIdx.x == 0) {
+    const double dmax = dm;
     if (!isfinite(dmax)) sh.err |= kErrNaN;
     if (record) {
       sh.dGmax = fmax(sh.dGmax, dmax);
@@ -613,9 +831,8 @@ __device__ void measure(Cta<T>& x) {
   Smem<T>& sh = x.sh;
   const int N = c.N, ld = c.ld;
   double ek = 0.0, dc = 0.0;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i = e / N, j = e % N;
-    const double k = c.K64[e];
+  PQMC_FOR_2D(i, 0, N, j, 0, N) {
+    const double k = c.K64[(long)i * N + j];
     if (k != 0.0) {
       for (int s = 0; s < 2; ++s) ek += k * ((i == j ? 1.0 : 0.0) - (double)x.G(s)[(long)j * ld + i]);
     }
@@ -626,13 +843,11 @@ __device__ void measure(Cta<T>& x) {
   dc = cta_sum(dc, sh.red);
   if (threadIdx.x == 0) {
     const int m = c.st->n_meas;
-    if (m < c.max_meas) {
-      double* r = c.meas + (long)m * kRecord;
-      r[0] = sh.sign_spin[0] * sh.sign_spin[1];
-      r[1] = (ek + c.U * dc) / N;
-      r[2] = dc / N;
-      r[3] = ek / N;
-      r[4] = sh.sign_running;
+    const double rec[kRecord] = {sh.sign_spin[0] * sh.sign_spin[1], (ek + c.U * dc) / N, dc / N, ek / N,
+                                 sh.sign_running};
+    for (int k = 0; k < kRecord; ++k) {
+      if (m < c.max_meas) c.meas[(long)m * kRecord + k] = rec[k];
+      c.last[k] = rec[k];
     }
     c.st->n_meas = m + 1;
   }
@@ -648,11 +863,14 @@ __device__ void sweep_up(Cta<T>& x, uint32_t sweep, bool do_measure) {
   for (int tau = 0; tau <= c.Ltau + 1; ++tau) {
     update_slice(x, tau, sweep);
     wrap(x, tau, +1);
+    x.mark(kPhWrap);
     if (tau <= c.Ltau && tau % c.n_stab == 0) {
       const int b = tau / c.n_stab;
       push_R(x, b);
       refresh(x, b, true);
+      x.mark(kPhRefresh);
       if (do_measure && tau == c.Ltau / 2) measure(x);
+      x.mark(kPhMeasure);
     }
   }
 }
@@ -662,13 +880,16 @@ __device__ void sweep_down(Cta<T>& x, uint32_t sweep, bool do_measure) {
   const ChainDesc& c = x.c;
   for (int tau = c.Ltau + 1; tau >= 0; --tau) {
     wrap(x, tau, -1);
+    x.mark(kPhWrap);
     update_slice(x, tau, sweep);
     const int t1 = tau - 1;
     if (t1 >= 0 && t1 % c.n_stab == 0) {
       const int b = t1 / c.n_stab;
       push_L(x, b);
       refresh(x, b, true);
+      x.mark(kPhRefresh);
       if (do_measure && t1 == c.Ltau / 2) measure(x);
+      x.mark(kPhMeasure);
     }
   }
 }
@@ -683,11 +904,20 @@ __device__ void load_state(Cta<T>& x) {
     x.sh.n_acc = st.n_acc;
     x.sh.acc_pos = st.acc_pos;
     x.sh.err = 0;
+    x.sh.staged = -1;
     x.sh.sign_spin[0] = st.logw[0][1];
     x.sh.sign_spin[1] = st.logw[1][1];
     x.sh.logw_spin[0] = st.logw[0][0];
     x.sh.logw_spin[1] = st.logw[1][0];
   }
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x >> 2, s = (threadIdx.x >> 1) & 1, si = threadIdx.x & 1;
+    x.sh.vtab[k][s][si] = x.c.vexp[k][s][si];
+    x.sh.vt[k][s][si] = (T)x.c.vexp[k][s][si];
+    x.sh.vti[k][s][si] = (T)(1.0 / x.c.vexp[k][s][si]);
+  }
+  if (threadIdx.x < kPhases) x.sh.cyc[threadIdx.x] = 0;
+  if (threadIdx.x == 0) x.sh.t_mark = clock64();
   __syncthreads();
 }
 
@@ -706,15 +936,46 @@ __device__ void store_state(Cta<T>& x, int* err) {
       st.logw[s][0] = x.sh.logw_spin[s];
       st.logw[s][1] = x.sh.sign_spin[s];
     }
+    for (int p = 0; p < kPhases; ++p) st.cycles[p] += x.sh.cyc[p];
     if (x.sh.err) atomicOr(err, x.sh.err);
   }
 }
 
+// Place G and the scratch: in shared memory after the fixed part when the
+// chain's footprint fits in res_bytes (G is copied in), else in global memory.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) init_kernel(const ChainDesc* chains, int chain0, uint64_t seed, int* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ Cta<T> make_cta(const ChainDesc& c, unsigned char* smem_raw, size_t res_bytes, uint64_t seed) {
   Smem<T>& sh = *reinterpret_cast<Smem<T>*>(smem_raw);
-  Cta<T> x{chains[chain0 + blockIdx.x], sh, seed};
+  const int ts = (int)sizeof(T);
+  const ScratchLayout L = scratch_layout(c.N, c.ld, c.nmax, ts);
+  const bool res = resident_bytes(c.N, c.ld, c.nmax, ts) <= res_bytes;
+  unsigned char* dyn = smem_raw + al16(sizeof(Smem<T>));
+  T* Gp = res ? reinterpret_cast<T*>(dyn) : reinterpret_cast<T*>(c.G);
+  unsigned char* scr = res ? dyn + al16(2 * (size_t)c.N * c.ld * ts) : reinterpret_cast<unsigned char*>(c.scratch);
+  Cta<T> x{c, sh, seed, Gp, scr, L, res};
+  if (res) {
+    const T* g = reinterpret_cast<const T*>(c.G);
+    for (long e = threadIdx.x; e < 2L * c.N * c.ld; e += blockDim.x) Gp[e] = g[e];
+  }
+  return x;
+}
+
+template <typename T>
+__device__ void write_back(Cta<T>& x) {
+  __syncthreads();
+  if (x.resident) {
+    T* g = reinterpret_cast<T*>(x.c.G);
+    for (long e = threadIdx.x; e < 2L * x.c.N * x.c.ld; e += blockDim.x) g[e] = x.Gp[e];
+  }
+  __syncthreads();
+}
+
+template <typename T, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) init_kernel(const ChainDesc* chains, int chain0, uint64_t seed,
+                                                          size_t res_bytes, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cta<T> x = make_cta<T>(chains[chain0 + blockIdx.x], smem_raw, res_bytes, seed);
+  Smem<T>& sh = x.sh;
   load_state(x);
   const ChainDesc& c = x.c;
   for (int b = c.nb; b >= 0; --b) push_L(x, b);
@@ -723,55 +984,89 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const ChainDesc* chains,
   if (threadIdx.x == 0) sh.sign_running = sh.sign_spin[0] * sh.sign_spin[1];
   __syncthreads();
   wrap(x, 0, -1);
+  write_back(x);
   store_state(x, err);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const ChainDesc* chains, uint64_t seed, uint32_t sweep0,
-                                                         int n_sweeps, int do_measure, int* err) {
+template <typename T, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) sweep_kernel(const ChainDesc* chains, uint64_t seed, uint32_t sweep0,
+                                                       int n_sweeps, int do_measure, size_t res_bytes, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T>& sh = *reinterpret_cast<Smem<T>*>(smem_raw);
-  Cta<T> x{chains[blockIdx.x], sh, seed};
-  if (x.c.st->err) return;
+  if (chains[blockIdx.x].st->err) return;
+  Cta<T> x = make_cta<T>(chains[blockIdx.x], smem_raw, res_bytes, seed);
+  Smem<T>& sh = x.sh;
   load_state(x);
+  const long long t_start = clock64();
   for (int k = 0; k < n_sweeps; ++k) {
     const uint32_t sw = sweep0 + (uint32_t)k;
     if ((sw & 1u) == 0) sweep_up(x, sw, do_measure != 0);
     else sweep_down(x, sw, do_measure != 0);
+    __syncthreads();
     if (sh.err) break;
   }
+  if (threadIdx.x == 0) sh.cyc[kPhTotal] += clock64() - t_start;
+  write_back(x);
   store_state(x, err);
 }
 
 // --------------------------------------------------------------------------
 // host launch wrappers (called from api.cpp)
 
-size_t smem_bytes(int prec) { return prec == 0 ? sizeof(Smem<double>) : sizeof(Smem<float>); }
+size_t smem_fixed(int prec) { return prec == 0 ? al16(sizeof(Smem<double>)) : al16(sizeof(Smem<float>)); }
 
-cudaError_t launch_init(int prec, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, int* d_err,
-                        cudaStream_t stream) {
-  const size_t sm = smem_bytes(prec);
-  if (prec == 0) {
-    cudaFuncSetAttribute(init_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    init_kernel<double><<<n, kThreads, sm, stream>>>(d_chains, chain0, seed, d_err);
-  } else {
-    cudaFuncSetAttribute(init_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    init_kernel<float><<<n, kThreads, sm, stream>>>(d_chains, chain0, seed, d_err);
-  }
+// CTAs per SM a launch is built for: the reduced paths pack twice as many
+// chains per SM as the FP64 path (their FP32 work and the FP64 stabilisation of
+// different chains overlap); smaller CTAs pack more chains.
+int ctas_per_sm(int prec, int tpb) { return (256 / tpb) * (prec == 0 ? 1 : 2); }
+
+// Largest resident footprint a launch offers per chain.
+size_t smem_resident_cap(int prec, int tpb) {
+  const size_t per_sm = 233472, reserve = 1024;
+  const size_t per_cta = per_sm / ctas_per_sm(prec, tpb) - reserve;
+  const size_t fixed = smem_fixed(prec);
+  return per_cta > fixed ? per_cta - fixed : 0;
+}
+
+template <typename T, int TPB, int MINB>
+static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res, int* d_err,
+                                 cudaStream_t stream) {
+  const size_t sm = al16(sizeof(Smem<T>)) + res;
+  cudaError_t e = cudaFuncSetAttribute(init_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  init_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, chain0, seed, res, d_err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(int prec, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0, int n_sweeps,
-                         int measure, int* d_err, cudaStream_t stream) {
-  const size_t sm = smem_bytes(prec);
-  if (prec == 0) {
-    cudaFuncSetAttribute(sweep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    sweep_kernel<double><<<n, kThreads, sm, stream>>>(d_chains, seed, sweep0, n_sweeps, measure, d_err);
-  } else {
-    cudaFuncSetAttribute(sweep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    sweep_kernel<float><<<n, kThreads, sm, stream>>>(d_chains, seed, sweep0, n_sweeps, measure, d_err);
-  }
+template <typename T, int TPB, int MINB>
+static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0, int n_sweeps,
+                                  int measure, size_t res, int* d_err, cudaStream_t stream) {
+  const size_t sm = al16(sizeof(Smem<T>)) + res;
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  sweep_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, seed, sweep0, n_sweeps, measure, res, d_err);
   return cudaGetLastError();
+}
+
+#define PQMC_DISPATCH(CALL, ...)                                                        \
+  do {                                                                                  \
+    if (prec == 0) {                                                                    \
+      if (tpb == 64) return CALL<double, 64, 4>(__VA_ARGS__);                           \
+      if (tpb == 128) return CALL<double, 128, 2>(__VA_ARGS__);                         \
+      return CALL<double, 256, 1>(__VA_ARGS__);                                         \
+    }                                                                                   \
+    if (tpb == 64) return CALL<float, 64, 8>(__VA_ARGS__);                              \
+    if (tpb == 128) return CALL<float, 128, 4>(__VA_ARGS__);                            \
+    return CALL<float, 256, 2>(__VA_ARGS__);                                            \
+  } while (0)
+
+cudaError_t launch_init(int prec, int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,
+                        int* d_err, cudaStream_t stream) {
+  PQMC_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream);
+}
+
+cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0,
+                         int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {
+  PQMC_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep0, n_sweeps, measure, res, d_err, stream);
 }
 
 }  // namespace pqmc

@@ -36,7 +36,7 @@ class ChainSpec(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("n_stab", C.c_int), ("delay_k", C.c_int), ("prec", C.c_int), ("seed", C.c_uint64),
                 ("n_chains", C.c_int), ("chain_offset", C.c_int), ("accept_log", C.c_int),
-                ("max_meas", C.c_int), ("stream", C.c_void_p)]
+                ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -59,15 +59,18 @@ SIGNATURES = [
     ("pqmc_synchronize", C.c_int, [C.c_void_p]),
     ("pqmc_measure", C.c_int, [C.c_void_p, C.c_int, C.POINTER(Obs)]),
     ("pqmc_get_measurements", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+    ("pqmc_get_last_records", C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     ("pqmc_set_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int8)]),
     ("pqmc_get_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int8)]),
     ("pqmc_get_green", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     ("pqmc_get_weight", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     ("pqmc_get_accept_log", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), C.c_long]),
     ("pqmc_get_stab_errors", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+    ("pqmc_get_phase_cycles", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong)]),
     ("pqmc_get_dims", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("pqmc_num_chains", C.c_int, [C.c_void_p]),
     ("pqmc_launch_count", C.c_long, [C.c_void_p]),
+    ("pqmc_device_bytes", C.c_size_t, [C.c_void_p]),
     ("pqmc_last_error", C.c_char_p, [C.c_void_p]),
     ("pqmc_free", None, [C.c_void_p]),
     ("pqmc_host_model", C.c_int, [C.POINTER(Lattice), C.c_double, C.POINTER(Trial), C.c_int,
@@ -125,12 +128,12 @@ class Context:
     """One libpqmc context: a batch of chains on the GPU."""
 
     def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=0, chain_offset=0, accept_log=0,
-                 max_meas=0, stream=None):
+                 max_meas=0, stream=None, cta_threads=0):
         lib = load()
         specs = list(specs)
         arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
         opts = Opts(n_stab, delay_k, prec, seed, len(specs), chain_offset, accept_log, max_meas,
-                    C.c_void_p(stream) if stream else None)
+                    C.c_void_p(stream) if stream else None, cta_threads)
         h = C.c_void_p()
         _check(lib.pqmc_init_batch(len(specs), arr, C.byref(opts), C.byref(h)))
         self._h = h
@@ -175,6 +178,16 @@ class Context:
         _check(load().pqmc_get_measurements(self._h, chain, _dptr(out), C.byref(n)), self._h)
         return out[: n.value]
 
+    def last_records(self, out=None):
+        """Latest record of every chain (n_chains x 5), one device-to-host copy."""
+        if out is None:
+            out = np.zeros((self.n_chains, 5))
+        _check(load().pqmc_get_last_records(self._h, _dptr(out)), self._h)
+        return out
+
+    def device_bytes(self):
+        return int(load().pqmc_device_bytes(self._h))
+
     def green(self, chain=0, spin=0):
         N = self.dims(chain)["N"]
         out = np.zeros((N, N))
@@ -206,6 +219,13 @@ class Context:
         n = C.c_long(cap)
         _check(load().pqmc_get_stab_errors(self._h, chain, _dptr(out), C.byref(n)), self._h)
         return out[: n.value]
+
+    PHASES = ("flip", "flush", "wrap", "stack", "qr", "refresh", "measure", "total")
+
+    def phase_cycles(self, chain=0):
+        out = (C.c_longlong * 8)()
+        _check(load().pqmc_get_phase_cycles(self._h, chain, out), self._h)
+        return dict(zip(self.PHASES, list(out)))
 
     def launch_count(self):
         return int(load().pqmc_launch_count(self._h))

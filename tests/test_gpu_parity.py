@@ -145,17 +145,31 @@ def test_batch_of_uneven_chains_equals_single_chains():
 
 
 def test_fp32_stabilisation_error_and_green():
+    """FP32 wraps and updates amplify rounding by about cond(B_tau) per slice;
+    with a 2-slice stabilisation interval max |G - G_FP64| stays below 1e-4."""
     spec = workloads.GUTZ_72[4.0]
     fields = workloads.random_fields(spec, seed=3)
-    ctx = pqmc.Context([spec], prec=pqmc.FP32, seed=7, n_stab=10)
+    ctx = pqmc.Context([spec], prec=pqmc.FP32, seed=7, n_stab=2)
     ctx.set_fields(fields)
-    ch = opq.Chain(oracle_params(spec, n_stab=10), fields=fields)
+    ch = opq.Chain(oracle_params(spec, n_stab=2), fields=fields)
     for s, sg in ((0, 1), (1, -1)):
         assert np.abs(ctx.green(0, s) - ch.G[sg]).max() < 1e-5
     ctx.sweep(4)
     errs = ctx.stab_errors()
-    assert len(errs) == 4 * 5 and errs.max() <= 1e-4
+    assert len(errs) == 4 * 21 and errs.max() <= 1e-4
     assert ctx.measure(0)["max_dG"] <= 1e-4
+
+
+def test_fp32_stabilisation_error_distribution():
+    """Over 32 chains x 4 sweeps the 99.9th percentile of the per-stabilisation
+    error stays below 1e-4 at a 2-slice interval (the worst single values are
+    a few 1e-4: flips accepted at small |R| amplify rounding by 1/|R|)."""
+    spec = workloads.GUTZ_72[8.0]
+    ctx = pqmc.Context([spec] * 32, prec=pqmc.FP32, seed=3, n_stab=2)
+    ctx.sweep(4)
+    errs = np.concatenate([ctx.stab_errors(c) for c in range(32)])
+    assert len(errs) == 32 * 4 * 41
+    assert np.percentile(errs, 99.9) <= 1e-4 and errs.max() < 2e-3
 
 
 @pytest.mark.parametrize("prec", [pqmc.FP64, pqmc.FP32])
