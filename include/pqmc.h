@@ -236,6 +236,38 @@ pqmc_status pqmc_host_model(const pqmc_lattice* lattice, double dtau, const pqmc
  * Exposed for tests. */
 pqmc_status pqmc_host_eigh(int n, const double* A, double* w, double* V);
 
+/* Allocation-free initialisation of one chain.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory, for example code that runs inside a host
+ * application whose device memory is reserved up front by its own allocator,
+ * or a loop that must not call cudaMalloc because of the implicit device
+ * synchronisation and the failure mode it brings.  It computes, for the FP64
+ * path, what pqmc_init_batch + pqmc_set_fields + pqmc_get_green /
+ * pqmc_get_weight compute for one chain: the left stack and G at tau = -1
+ * for the given fields, with the same kernel.
+ *
+ *   spec     host pointer, one chain (validated as in pqmc_init_batch)
+ *   n_stab   slices between QR stabilisations (Ltau/2 must be a multiple)
+ *   d_fields device pointer, (Ltau+2) x N int8 fields in {-1,+1}, read only
+ *   d_G      device pointer, output, 2 x N x N FP64: G_up then G_dn, row-major
+ *   d_logw   device pointer, output, 4 FP64: (logabs_up, sign_up, logabs_dn, sign_dn)
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream)
+ *
+ * It allocates no device memory: every other buffer the kernel uses lives in
+ * one 16 MiB array in the library's device image, which every GPU that loads
+ * the library holds until the process exits.  A chain needing more than
+ * 16 MiB (roughly N > 128 at Ltau = 200, n_stab = 10) is rejected with
+ * PQMC_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * re-initialises what it reads), so calls that overlap on the GPU, from any
+ * stream or thread, race: serialise them.  The call synchronises `stream`
+ * before it returns and reports PQMC_ESTAB / PQMC_ENAN / PQMC_ECUDA like the
+ * other entry points (message: pqmc_last_error(NULL)). */
+pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_stab, const int8_t* d_fields,
+                               double* d_G, double* d_logw, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

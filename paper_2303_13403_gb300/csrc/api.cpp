@@ -90,7 +90,12 @@ std::string lattice_key(const pqmc_chain_spec& s) {
   return buf;
 }
 
-pqmc_status check_spec(const pqmc_chain_spec& s, const pqmc_opts& o, std::string& why) {
+}  // namespace
+
+namespace pqmc {
+void set_init_error(const std::string& msg) { g_init_error = msg; }
+
+pqmc_status check_spec(const pqmc_chain_spec& s, int n_stab, std::string& why) {
   const auto& l = s.lattice;
   if (l.kind != PQMC_HONEYCOMB && l.kind != PQMC_SQUARE) { why = "unknown lattice kind"; return PQMC_EINVAL; }
   if (l.Lx < 1 || l.Ly < 1 || l.Lx > 64 || l.Ly > 64) { why = "lattice extent out of range"; return PQMC_EINVAL; }
@@ -108,9 +113,12 @@ pqmc_status check_spec(const pqmc_chain_spec& s, const pqmc_opts& o, std::string
   const int Ltau = (int)std::lround(lt);
   if (std::fabs(lt - Ltau) > 1e-9 * std::max(1.0, lt)) { why = "two_theta / dtau is not an integer"; return PQMC_EINVAL; }
   if (Ltau % 2) { why = "Ltau must be even"; return PQMC_EINVAL; }
-  if (o.n_stab < 1 || (Ltau / 2) % o.n_stab) { why = "Ltau/2 must be a multiple of n_stab"; return PQMC_EINVAL; }
+  if (n_stab < 1 || (Ltau / 2) % n_stab) { why = "Ltau/2 must be a multiple of n_stab"; return PQMC_EINVAL; }
   return PQMC_OK;
 }
+}  // namespace pqmc
+
+namespace {
 
 template <typename T>
 void put(std::vector<unsigned char>& a, size_t off, const std::vector<double>& src, int rows, int cols, int ld) {
@@ -155,7 +163,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     return fail(nullptr, PQMC_EINVAL, "cta_threads must be 0, 64, 128 or 256");
   for (int c = 0; c < n; ++c) {
     std::string why;
-    if (check_spec(specs[c], o, why) != PQMC_OK) return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
+    if (check_spec(specs[c], o.n_stab, why) != PQMC_OK) return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
   }
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)

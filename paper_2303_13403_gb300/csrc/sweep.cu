@@ -24,9 +24,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
 #include <type_traits>
+#include <vector>
 
+#include "../../include/pqmc.h"
 #include "chain.h"
+#include "model.h"
 #include "philox.cuh"
 
 namespace pqmc {
@@ -1069,4 +1076,195 @@ cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, ui
   PQMC_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep0, n_sweeps, measure, res, d_err, stream);
 }
 
+// --------------------------------------------------------------------------
+// Allocation-free initialisation of one chain (pqmc_green_noalloc).
+//
+// Runs init_kernel for a single FP64 chain with every buffer the kernel needs
+// (its descriptor and counters, the model tables, the left/right stacks, G
+// and the phase scratch) placed in one file-scope device array instead of
+// memory obtained from cudaMalloc.  The caller supplies the fields and the
+// output buffers.  Host code never uses the array's name as an address: the
+// device address comes from cudaGetSymbolAddress, once per device.
+
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+pqmc_status check_spec(const pqmc_chain_spec& s, int n_stab, std::string& why);
+void set_init_error(const std::string& msg);
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256];
+bool g_noalloc_ready[256];
+
+size_t take256(size_t& off, size_t bytes) {
+  const size_t at = off;
+  off = (off + bytes + 255) & ~(size_t)255;
+  return at;
+}
+}  // namespace
+
 }  // namespace pqmc
+
+extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_stab, const int8_t* d_fields,
+                                          double* d_G, double* d_logw, void* stream) {
+  using namespace pqmc;
+  if (!spec || !d_fields || !d_G || !d_logw) {
+    set_init_error("pqmc_green_noalloc: NULL argument");
+    return PQMC_EINVAL;
+  }
+  std::string why;
+  if (check_spec(*spec, n_stab, why) != PQMC_OK) {
+    set_init_error("pqmc_green_noalloc: " + why);
+    return PQMC_EINVAL;
+  }
+  const pqmc_lattice& lt = spec->lattice;
+  const int N = lt.kind == PQMC_HONEYCOMB ? 2 * lt.Lx * lt.Ly : lt.Lx * lt.Ly;
+  const int ld = (N + 3) & ~3;
+  const int nup = spec->trial.N_up < 0 ? N / 2 : spec->trial.N_up;
+  const int ndn = spec->trial.N_dn < 0 ? N / 2 : spec->trial.N_dn;
+  const int nmax = nup > ndn ? nup : ndn;
+  const int Ltau = (int)std::lround(spec->two_theta / spec->dtau);
+  const int nb = Ltau / n_stab;
+  const size_t blk = (size_t)N * nmax * 8;
+
+  // layout inside the static array
+  size_t off = 0;
+  const size_t o_desc = take256(off, sizeof(ChainDesc));
+  const size_t o_state = take256(off, sizeof(ChainState));
+  const size_t o_err = take256(off, sizeof(int));
+  const size_t o_em = take256(off, (size_t)N * ld * 8);
+  const size_t o_ep = take256(off, (size_t)N * ld * 8);
+  const size_t o_em64 = take256(off, (size_t)N * N * 8);
+  const size_t o_k64 = take256(off, (size_t)N * N * 8);
+  const size_t o_P = take256(off, 2 * blk);
+  const size_t upload = off;                   // everything above is uploaded each call
+  const size_t o_rst = take256(off, (size_t)(nb + 1) * 2 * blk);
+  const size_t o_lst = take256(off, (size_t)(nb + 1) * 2 * blk);
+  const size_t o_rlog = take256(off, (size_t)(nb + 1) * 4 * 8);
+  const size_t o_llog = take256(off, (size_t)(nb + 1) * 4 * 8);
+  const size_t o_G = take256(off, 2 * (size_t)N * ld * 8);
+  const size_t o_scr = take256(off, scratch_layout(N, ld, nmax, 8).total);
+  if (off > kNoAllocBytes) {
+    set_init_error("pqmc_green_noalloc: chain needs " + std::to_string(off) + " bytes, above the 16 MiB maximum");
+    return PQMC_EINVAL;
+  }
+
+  // device address of the array, looked up once per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    set_init_error(std::string("pqmc_green_noalloc: no current device: ") + cudaGetErrorString(e));
+    return PQMC_ECUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ready[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || p == nullptr) {
+        set_init_error(std::string("pqmc_green_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        return PQMC_ECUDA;
+      }
+      g_noalloc_addr[dev] = p;
+      g_noalloc_ready[dev] = true;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  }
+
+  // host model set-up (FP64), same as context creation
+  Lattice lat{lt.kind, lt.Lx, lt.Ly, lt.t, lt.tp};
+  std::vector<double> K, eps, w, V, em, ep, P[2];
+  build_hopping(lat, K, eps);
+  if (!sym_eig(N, K, w, V)) {
+    set_init_error("pqmc_green_noalloc: eigensolver failed on K");
+    return PQMC_EINVAL;
+  }
+  expm_from_eig(N, w, V, -spec->dtau, em);
+  expm_from_eig(N, w, V, +spec->dtau, ep);
+  for (int sp = 0; sp < 2; ++sp) {
+    double gap = 0;
+    if (!trial_orbitals(lat, K, eps, spec->trial.M_N, spec->trial.tiebreak, sp == 0 ? 1 : -1, sp == 0 ? nup : ndn,
+                        P[sp], gap) || !(gap > 1e-8)) {
+      set_init_error("pqmc_green_noalloc: trial orbitals failed or open shell");
+      return PQMC_EINVAL;
+    }
+  }
+
+  // contents of the uploaded prefix; counters start from zero every call
+  std::vector<unsigned char> h(upload, 0);
+  ChainDesc d;
+  memset(&d, 0, sizeof d);
+  d.N = N; d.ld = ld; d.nup = nup; d.ndn = ndn; d.nmax = nmax;
+  d.Ltau = Ltau; d.nb = nb; d.n_stab = n_stab; d.kb = kBlock;
+  d.U = spec->U;
+  const double kap[2] = {hs_coupling(spec->dtau * spec->U), hs_coupling(spec->trial.g)};
+  for (int k = 0; k < 2; ++k)
+    for (int sp = 0; sp < 2; ++sp)
+      for (int si = 0; si < 2; ++si) {
+        const double sigma = sp == 0 ? 1.0 : -1.0, sv = si == 0 ? 1.0 : -1.0;
+        d.delta[k][sp][si] = std::exp(-2.0 * sigma * kap[k] * sv) - 1.0;
+        d.vexp[k][sp][si] = std::exp(sigma * kap[k] * sv);
+      }
+  d.fields = const_cast<int8_t*>(d_fields);
+  d.G = base + o_G;
+  d.expKm = base + o_em;
+  d.expKp = base + o_ep;
+  d.expKm64 = reinterpret_cast<const double*>(base + o_em64);
+  d.K64 = reinterpret_cast<const double*>(base + o_k64);
+  d.P = reinterpret_cast<const double*>(base + o_P);
+  d.Rst = reinterpret_cast<double*>(base + o_rst);
+  d.Lst = reinterpret_cast<double*>(base + o_lst);
+  d.Rlog = reinterpret_cast<double*>(base + o_rlog);
+  d.Llog = reinterpret_cast<double*>(base + o_llog);
+  d.scratch = base + o_scr;
+  d.st = reinterpret_cast<ChainState*>(base + o_state);
+  memcpy(h.data() + o_desc, &d, sizeof d);
+  ChainState st{};
+  st.sign_running = 1.0;
+  st.logw[0][1] = st.logw[1][1] = 1.0;
+  memcpy(h.data() + o_state, &st, sizeof st);
+  double* hem = reinterpret_cast<double*>(h.data() + o_em);
+  double* hep = reinterpret_cast<double*>(h.data() + o_ep);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      hem[(size_t)i * ld + j] = em[(size_t)i * N + j];
+      hep[(size_t)i * ld + j] = ep[(size_t)i * N + j];
+    }
+  memcpy(h.data() + o_em64, em.data(), (size_t)N * N * 8);
+  memcpy(h.data() + o_k64, K.data(), (size_t)N * N * 8);
+  double* hP = reinterpret_cast<double*>(h.data() + o_P);
+  for (int sp = 0; sp < 2; ++sp) {
+    const int ns = sp == 0 ? nup : ndn;
+    for (int i = 0; i < N; ++i)
+      for (int k = 0; k < ns; ++k) hP[(size_t)sp * N * nmax + (size_t)k * N + i] = P[sp][(size_t)i * ns + k];
+  }
+
+  cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+  e = cudaMemcpyAsync(base, h.data(), upload, cudaMemcpyHostToDevice, st_);
+  if (e == cudaSuccess) {
+    const size_t cap = smem_resident_cap(0, 256);
+    const size_t rb = resident_bytes(N, ld, nmax, 8);
+    e = launch_init_t<double, 256, 1>(reinterpret_cast<const ChainDesc*>(base + o_desc), 0, 1, 0,
+                                      rb <= cap ? rb : 0, reinterpret_cast<int*>(base + o_err), st_);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(d_G, (size_t)N * 8, base + o_G, (size_t)ld * 8, (size_t)N * 8, 2 * (size_t)N,
+                          cudaMemcpyDeviceToDevice, st_);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_logw, base + o_state + offsetof(ChainState, logw), 4 * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st_);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, base + o_err, sizeof(int), cudaMemcpyDeviceToHost, st_);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
+  if (e != cudaSuccess) {
+    set_init_error(std::string("pqmc_green_noalloc: ") + cudaGetErrorString(e));
+    return PQMC_ECUDA;
+  }
+  if (herr) {
+    set_init_error((herr & kErrNaN) ? "pqmc_green_noalloc: NaN or Inf in G" : "pqmc_green_noalloc: singular matrix");
+    return (herr & kErrNaN) ? PQMC_ENAN : PQMC_ESTAB;
+  }
+  return PQMC_OK;
+}

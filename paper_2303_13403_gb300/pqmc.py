@@ -77,6 +77,8 @@ SIGNATURES = [
                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
     ("pqmc_host_eigh", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("pqmc_green_noalloc", C.c_int, [C.POINTER(ChainSpec), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
 ]
 
 
@@ -255,3 +257,10 @@ def host_eigh(A):
     V = np.zeros((n, n))
     _check(lib.pqmc_host_eigh(n, _dptr(A), _dptr(w), _dptr(V)))
     return w, V
+
+
+def green_noalloc(spec, n_stab, d_fields, d_G, d_logw, stream=None):
+    """pqmc_green_noalloc: device pointers (ints) in and out; no device allocation."""
+    cs = chain_spec_of(spec)
+    _check(load().pqmc_green_noalloc(C.byref(cs), n_stab, C.c_void_p(d_fields), C.c_void_p(d_G),
+                                     C.c_void_p(d_logw), C.c_void_p(stream) if stream else None))
