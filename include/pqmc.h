@@ -196,9 +196,10 @@ pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);
 pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n);
 
 /* SM clock cycles one chain's CTA has spent, as seen by its thread 0, in
- * each phase of its sweeps so far: out[0..7] = (flip decisions, delayed-update
- * flushes, slice wrapping, stack slice products, Householder QR, G refresh
- * from the stacks, measurement, total). */
+ * each phase of its sweeps so far: out[0..11] = (flip decisions,
+ * delayed-update flushes, slice wrapping, stack slice products, QR
+ * factorisation, rest of the G refresh, measurement, total, forming Q,
+ * Q_L^T Q_R, its LU inverse, G assembly). */
 pqmc_status pqmc_get_phase_cycles(pqmc_ctx* ctx, int chain, long long* out);
 
 /* Sizes of one chain: out[0..5] = (N, N_up, N_dn, Ltau, n_stab, delay_k). */

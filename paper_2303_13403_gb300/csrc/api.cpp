@@ -154,7 +154,6 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (n < 1 || !specs || !opts) return fail(nullptr, PQMC_EINVAL, "need n >= 1, specs and opts");
   pqmc_opts o = *opts;
   if (o.prec < PQMC_FP64 || o.prec > PQMC_BF16X3) return fail(nullptr, PQMC_EINVAL, "unknown precision");
-  if (o.prec == PQMC_BF16X3) return fail(nullptr, PQMC_EINVAL, "BF16X3 path not available in this build");
   if (o.delay_k == 0) o.delay_k = kBlock;
   if (o.delay_k != kBlock) return fail(nullptr, PQMC_EINVAL, "delay_k must be 0 or 32");
   if (o.max_meas <= 0) o.max_meas = 4096;
@@ -317,6 +316,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.N = h.N; d.ld = h.ld; d.nup = h.nup; d.ndn = h.ndn; d.nmax = h.nmax;
     d.Ltau = h.Ltau; d.nb = h.nb; d.n_stab = o.n_stab; d.kb = o.delay_k;
     d.chain_index = (uint32_t)(o.chain_offset + c);
+    d.tc = ctx->prec == PQMC_BF16X3 ? 1 : 0;
     d.U = s.U;
     const double kap[2] = {hs_coupling(s.dtau * s.U), hs_coupling(s.trial.g)};
     for (int k = 0; k < 2; ++k)

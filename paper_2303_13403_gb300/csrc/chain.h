@@ -14,7 +14,10 @@ constexpr int kRecord = 5;        // doubles per measurement record
 constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
 
 // phases timed with clock64() by thread 0 of each chain CTA
-enum : int { kPhFlip = 0, kPhFlush, kPhWrap, kPhStack, kPhQR, kPhRefresh, kPhMeasure, kPhTotal, kPhases };
+enum : int {
+  kPhFlip = 0, kPhFlush, kPhWrap, kPhStack, kPhQR, kPhRefresh, kPhMeasure, kPhTotal,
+  kPhQRForm, kPhOverlap, kPhLU, kPhAssemble, kPhases
+};
 
 // error bits written by the kernels
 enum : int { kErrNaN = 1, kErrStab = 2, kErrTimeout = 4 };
@@ -43,6 +46,7 @@ struct ChainDesc {
   int N, ld, nup, ndn, nmax;
   int Ltau, nb, n_stab, kb;
   uint32_t chain_index;
+  int tc;                  // 1: wrap and delayed-update GEMMs as split BF16 tensor-core products
   double U;
   double delta[2][2][2];   // [0 Hubbard, 1 Gutzwiller][spin][s=+1 -> 0, s=-1 -> 1]: e^{-2 sigma kappa s} - 1
   double vexp[2][2][2];    // same indexing: e^{sigma kappa s}
@@ -82,17 +86,24 @@ namespace pqmc {
 // Byte offsets of the phase buffers inside one chain's scratch region.  The
 // phases never overlap in time, so their buffers share the region:
 //   wrap    : Gt (N x ld, T) for one spin at a time
-//   flush   : U (kBlock x N, T) and W (kBlock x ld, T) for one spin
+//   flips   : A_S (N x kBlock, T), W and M W (kBlock x ld, T) for one spin,
+//             and the per-block flip buffers
 //   stack   : M64 (N x n, FP64, column-major), then a region holding the two
 //             path-precision product buffers Mt, Mt2 (N x n, T, row-major)
 //             and later the FP64 Q of the QR; Householder betas / R_jj
-//   refresh : O, X (n x n, FP64, both spins), Y (n x ld, T), Q_R and Q_L in the
+//   refresh : O (n x n, FP64, both spins, inverted in place), Y (n x ld, T), Q_R and Q_L in the
 //             path precision (N x n, T); LU pivots / multipliers
 struct ScratchLayout {
-  size_t gt, u, w, m64, mtq, mt2, qaux, o, x, y, qrt, qlt, laux, total;
+  size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, o, y, qrt, qlt, laux, total;
 };
 
 PQMC_HDI size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Per-block buffers of the flip phase (kBlock x kBlock blocks of both spins,
+// uniforms, accepted sites); the layout is FlipBuf<T> in sweep.cu.
+PQMC_HDI size_t flipbuf_bytes(int tsize) {
+  return al16(4 * (size_t)kBlock * (kBlock + 1) * tsize + 2 * (size_t)kBlock * tsize + (size_t)kBlock * (8 + 4 + 4 + 4));
+}
 
 PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   ScratchLayout L;
@@ -101,7 +112,9 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   size_t wrap = al16((size_t)N * ld * tsize);
   L.u = 0;
   L.w = al16((size_t)N * kBlock * tsize);
-  size_t flush = L.w + al16((size_t)kBlock * ld * tsize);
+  L.mw = L.w + al16((size_t)kBlock * ld * tsize);
+  L.fb = L.mw + al16((size_t)kBlock * ld * tsize);
+  size_t flush = L.fb + flipbuf_bytes(tsize);
   L.m64 = 0;
   L.mtq = al16(Nn * 8);
   L.mt2 = L.mtq + al16(Nn * tsize);
@@ -109,9 +122,8 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   const size_t mtq_sz = two_mt > al16(Nn * 8) ? two_mt : al16(Nn * 8);
   L.qaux = L.mtq + mtq_sz;
   size_t stack = L.qaux + al16((3 * (size_t)n + (size_t)kQRParts * n) * 8);
-  L.o = 0;                                   // O for spin 0, then spin 1
-  L.x = 2 * al16((size_t)n * n * 8);         // X for spin 0, then spin 1
-  L.y = L.x + 2 * al16((size_t)n * n * 8);
+  L.o = 0;                                   // O for spin 0, then spin 1 (inverted in place)
+  L.y = 2 * al16((size_t)n * n * 8);
   L.qrt = L.y + al16((size_t)n * ld * tsize);
   L.qlt = L.qrt + al16(Nn * tsize);
   L.laux = L.qlt + al16(Nn * tsize);
@@ -124,7 +136,8 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   return L;
 }
 
-// Shared-memory bytes of a chain that keeps G and its scratch resident.
+// Shared-memory bytes of a chain that keeps G and its scratch resident
+// (a chain that does not fit keeps only the flip buffers in shared memory).
 PQMC_HDI size_t resident_bytes(int N, int ld, int n, int tsize) {
   return al16(2 * (size_t)N * ld * tsize) + scratch_layout(N, ld, n, tsize).total;
 }

@@ -21,6 +21,7 @@
 // and the assembly of G from them.  The Householder QR of the stack blocks,
 // the product Q_L^T Q_R, its inverse and the log-determinant / sign are FP64
 // in every path.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -174,15 +175,103 @@ __device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, co
 }
 
 // --------------------------------------------------------------------------
+// Split-precision tensor-core GEMM (the BF16X3 path): C = A B for FP32 A, B
+// with every operand split as x = hi + lo, hi = bf16(x), lo = bf16(x - hi),
+// and C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 by
+// mma.sync.m16n8k16 (Henry, Tang & Heinecke 2019 use the same split).  Each
+// warp owns 16 x 8 output tiles; operands are read with arbitrary strides
+// (zero outside the matrix) and split on the fly.
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 first, __nv_bfloat16 second) {
+  return (uint32_t)__bfloat16_as_ushort(first) | ((uint32_t)__bfloat16_as_ushort(second) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <typename Epi>
+__device__ void cta_gemm_bf16x3(int M, int Nn, int K, const float* A, int sai, int sak, const float* B, int sbk,
+                                int sbj, float* C, int sci, int scj, Epi epi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane >> 2, tg = lane & 3;
+  const int tm = (M + 15) >> 4, tn = (Nn + 7) >> 3;
+  auto a_at = [&](int r, int k) -> float { return (r < M && k < K) ? A[(long)r * sai + (long)k * sak] : 0.0f; };
+  auto b_at = [&](int k, int n) -> float { return (k < K && n < Nn) ? B[(long)k * sbk + (long)n * sbj] : 0.0f; };
+  for (int t = warp; t < tm * tn; t += nw) {
+    const int m0 = (t / tn) << 4, n0 = (t % tn) << 3;
+    const int r0 = m0 + g, r1 = m0 + g + 8, nn = n0 + g;
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+      const int k = k0 + 2 * tg;
+      const float av[8] = {a_at(r0, k), a_at(r0, k + 1), a_at(r1, k), a_at(r1, k + 1),
+                           a_at(r0, k + 8), a_at(r0, k + 9), a_at(r1, k + 8), a_at(r1, k + 9)};
+      const float bv[4] = {b_at(k, nn), b_at(k + 1, nn), b_at(k + 8, nn), b_at(k + 9, nn)};
+      __nv_bfloat16 ah[8], al[8], bh[4], bl[4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) split_bf16(av[q], ah[q], al[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) split_bf16(bv[q], bh[q], bl[q]);
+      const uint32_t AH[4] = {pack2(ah[0], ah[1]), pack2(ah[2], ah[3]), pack2(ah[4], ah[5]), pack2(ah[6], ah[7])};
+      const uint32_t AL[4] = {pack2(al[0], al[1]), pack2(al[2], al[3]), pack2(al[4], al[5]), pack2(al[6], al[7])};
+      const uint32_t BH[2] = {pack2(bh[0], bh[1]), pack2(bh[2], bh[3])};
+      const uint32_t BL[2] = {pack2(bl[0], bl[1]), pack2(bl[2], bl[3])};
+      mma_bf16(c, AH, BL);
+      mma_bf16(c, AL, BH);
+      mma_bf16(c, AH, BH);
+    }
+    const int cc = n0 + 2 * tg;
+    if (r0 < M) {
+      if (cc < Nn) epi(C, sci, scj, r0, cc, c[0]);
+      if (cc + 1 < Nn) epi(C, sci, scj, r0, cc + 1, c[1]);
+    }
+    if (r1 < M) {
+      if (cc < Nn) epi(C, sci, scj, r1, cc, c[2]);
+      if (cc + 1 < Nn) epi(C, sci, scj, r1, cc + 1, c[3]);
+    }
+  }
+}
+
+// Path GEMM of the wrap and of the delayed update: split-precision tensor
+// cores when the chain runs the BF16X3 path, CUDA-core FMA otherwise.
+template <typename T, typename Epi>
+__device__ void path_gemm(const ChainDesc& c, int M, int Nn, int K, const T* A, int sai, int sak, const T* B, int sbk,
+                          int sbj, T* C, int sci, int scj, Epi epi) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c.tc) {
+      cta_gemm_bf16x3(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
+      return;
+    }
+  }
+  cta_gemm<T>(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
+}
+
+// --------------------------------------------------------------------------
 // shared memory of one chain CTA
 
+// Buffers of one flip block (lives in shared memory, see make_cta).
 template <typename T>
-struct Smem {
+struct FlipBuf {
   T Gb[2][kBlock][kBlock + 1];      // diagonal block of current G, both spins
   T Tu[2][kBlock][kBlock + 1];      // 1 + (1 - G_SS) Gamma, inverted in place, then M
   T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
   double u[kBlock];                 // Metropolis uniforms of the block
   float uf[kBlock];                 // the same rounded down to 24 bits (FP32 decisions)
+  int sites[kBlock];                // block index of each accepted flip
+  int fl[kBlock];                   // fields of the block
+};
+
+template <typename T>
+struct Smem {
   double red[32];                   // reduction scratch
   double vtab[2][2][2];             // e^{sigma kappa s}: [Gutzwiller?][spin][s = -1?]
   T vt[2][2][2];                    // the same in the path precision
@@ -190,8 +279,6 @@ struct Smem {
   long long cyc[kPhases];           // per-phase clock cycles (thread 0)
   long long t_mark;
   signed char fr[kMaxN];            // fields of the staged slice
-  int sites[kBlock];                // block index of each accepted flip
-  int fl[kBlock];                   // fields of the block
   int na;                           // accepted flips in the block
   int piv;
   int nswap[2];
@@ -215,6 +302,7 @@ struct Cta {
   unsigned char* scr;
   ScratchLayout L;
   bool resident;
+  FlipBuf<T>* fb;
   __device__ T* G(int s) const { return Gp + (long)s * c.N * c.ld; }
   __device__ T* Gt() const { return reinterpret_cast<T*>(scr + L.gt); }
   __device__ T* Ub() const { return reinterpret_cast<T*>(scr + L.u); }
@@ -229,9 +317,6 @@ struct Cta {
   __device__ double* qpart() const { return qbeta() + 3 * c.nmax; }
   __device__ double* Ob(int s) const {
     return reinterpret_cast<double*>(scr + L.o + s * al16((size_t)c.nmax * c.nmax * 8));
-  }
-  __device__ double* Xb(int s) const {
-    return reinterpret_cast<double*>(scr + L.x + s * al16((size_t)c.nmax * c.nmax * 8));
   }
   __device__ T* Yb() const { return reinterpret_cast<T*>(scr + L.y); }
   __device__ T* QRt() const { return reinterpret_cast<T*>(scr + L.qrt); }
@@ -290,6 +375,7 @@ template <typename T>
 __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const ChainDesc& c = x.c;
   Smem<T>& sh = x.sh;
+  FlipBuf<T>& fb = *x.fb;
   const int N = c.N, ld = c.ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int kap = x.gutz(tau) ? 1 : 0;
@@ -302,7 +388,7 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
     const int nbk = min(kBlock, N - i0);
     for (int e = threadIdx.x; e < 2 * kBlock * kBlock; e += blockDim.x) {
       const int s = e / (kBlock * kBlock), r = (e / kBlock) % kBlock, q = e % kBlock;
-      sh.Gb[s][r][q] = (r < nbk && q < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + q] : T(0);
+      fb.Gb[s][r][q] = (r < nbk && q < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + q] : T(0);
     }
     if (threadIdx.x < kBlock) {
       const int j = threadIdx.x;
@@ -310,25 +396,25 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
         const U4 w = philox4x32_10((uint32_t)(i0 + j), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
                                    (uint32_t)(x.seed >> 32));
         const uint64_t m53 = ((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11);
-        sh.u[j] = (double)m53 * 0x1.0p-53;
-        sh.uf[j] = (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;   // the same uniform rounded down to 24 bits
+        fb.u[j] = (double)m53 * 0x1.0p-53;
+        fb.uf[j] = (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;   // the same uniform rounded down to 24 bits
       } else {
-        sh.u[j] = 2.0;
-        sh.uf[j] = 2.0f;
+        fb.u[j] = 2.0;
+        fb.uf[j] = 2.0f;
       }
-      sh.fl[j] = j < nbk ? (int)f[i0 + j] : 1;
+      fb.fl[j] = j < nbk ? (int)f[i0 + j] : 1;
     }
     __syncthreads();
 
     if (warp == 0) {
       int a = 0;
       for (int j = 0; j < nbk; ++j) {
-        const int si = sh.fl[j] > 0 ? 0 : 1;
+        const int si = fb.fl[j] > 0 ? 0 : 1;
         const T d0 = dl[0][si], d1 = dl[1][si];
-        const T r0 = T(1) + d0 * (T(1) - sh.Gb[0][j][j]);
-        const T r1 = T(1) + d1 * (T(1) - sh.Gb[1][j][j]);
+        const T r0 = T(1) + d0 * (T(1) - fb.Gb[0][j][j]);
+        const T r1 = T(1) + d1 * (T(1) - fb.Gb[1][j][j]);
         const T R = r0 * r1;
-        const bool acc = metropolis_accept<T>(sh.u[j], sh.uf[j], R);
+        const bool acc = metropolis_accept<T>(fb.u[j], fb.uf[j], R);
         if (lane == 0) {
           if (!isfinite(R)) sh.err |= kErrNaN;
           if (sh.acc_pos < c.acc_cap) c.acc_log[sh.acc_pos] = acc ? 1 : 0;
@@ -338,19 +424,19 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
         if (!acc) continue;
         const T c0 = d0 / r0, c1 = d1 / r1;
         if (lane > j && lane < nbk) {
-          const T y0 = c0 * sh.Gb[0][j][lane], y1 = c1 * sh.Gb[1][j][lane];
+          const T y0 = c0 * fb.Gb[0][j][lane], y1 = c1 * fb.Gb[1][j][lane];
 #pragma unroll 4
           for (int r = j + 1; r < nbk; ++r) {
-            sh.Gb[0][r][lane] = fma(sh.Gb[0][r][j], y0, sh.Gb[0][r][lane]);
-            sh.Gb[1][r][lane] = fma(sh.Gb[1][r][j], y1, sh.Gb[1][r][lane]);
+            fb.Gb[0][r][lane] = fma(fb.Gb[0][r][j], y0, fb.Gb[0][r][lane]);
+            fb.Gb[1][r][lane] = fma(fb.Gb[1][r][j], y1, fb.Gb[1][r][lane]);
           }
         }
         if (lane == 0) {
-          sh.sites[a] = j;
-          sh.cl[0][a] = d0;
-          sh.cl[1][a] = d1;
-          sh.fl[j] = -sh.fl[j];
-          f[i0 + j] = (int8_t)sh.fl[j];
+          fb.sites[a] = j;
+          fb.cl[0][a] = d0;
+          fb.cl[1][a] = d1;
+          fb.fl[j] = -fb.fl[j];
+          f[i0 + j] = (int8_t)fb.fl[j];
           sh.sign_running *= (R < T(0)) ? -1.0 : 1.0;
           sh.n_acc++;
         }
@@ -368,13 +454,13 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
     // per spin; then M = Gamma X^{-1} (stored in Tu)
     PQMC_FOR_2D(sl, 0, 2 * a, m, 0, a) {
       const int s = sl >= a ? 1 : 0, l = sl - s * a;
-      const T g = x.G(s)[(long)(i0 + sh.sites[l]) * ld + i0 + sh.sites[m]];
-      sh.Tu[s][l][m] = ((l == m) ? T(1) : T(0)) + ((l == m ? T(1) : T(0)) - g) * sh.cl[s][m];
+      const T g = x.G(s)[(long)(i0 + fb.sites[l]) * ld + i0 + fb.sites[m]];
+      fb.Tu[s][l][m] = ((l == m) ? T(1) : T(0)) + ((l == m ? T(1) : T(0)) - g) * fb.cl[s][m];
     }
     __syncthreads();
     if (warp < 2) {
       const int s = warp;
-      T (*X)[kBlock + 1] = sh.Tu[s];
+      T (*X)[kBlock + 1] = fb.Tu[s];
       for (int p = 0; p < a; ++p) {
         const T ip = T(1) / X[p][p];
         const T xpl = lane < a ? X[p][lane] : T(0);
@@ -389,24 +475,23 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
         __syncwarp();
       }
       for (int l = 0; l < a; ++l)
-        if (lane < a) X[l][lane] *= sh.cl[s][l];
+        if (lane < a) X[l][lane] *= fb.cl[s][l];
     }
     __syncthreads();
-    // per spin: U[:, m] = sum_l (e_{s_l} - G[:, s_l]) M[l][m]  (N x a, column-major),
-    // W = G_{S,:} (a x N) read before G changes, then G -= U W
+    // per spin: A_S = E_S - G_{:,S} (N x a, column-major) and W = G_{S,:}
+    // (a x N) gathered before G changes, then MW = M W and G -= A_S MW
+    T* MW = reinterpret_cast<T*>(x.scr + x.L.mw);
     for (int s = 0; s < 2; ++s) {
       T* Gs = x.G(s);
       PQMC_FOR_2D(m, 0, a, i, 0, N) {
-        T acc = T(0);
-        for (int l = 0; l < a; ++l) {
-          const int col = i0 + sh.sites[l];
-          acc = fma((i == col ? T(1) : T(0)) - Gs[(long)i * ld + col], sh.Tu[s][l][m], acc);
-        }
-        Ubuf[(long)m * N + i] = acc;
+        const int col = i0 + fb.sites[m];
+        Ubuf[(long)m * N + i] = (i == col ? T(1) : T(0)) - Gs[(long)i * ld + col];
       }
-      PQMC_FOR_2D(l, 0, a, q, 0, N) Wbuf[(long)l * ld + q] = Gs[(long)(i0 + sh.sites[l]) * ld + q];
+      PQMC_FOR_2D(l, 0, a, q, 0, N) Wbuf[(long)l * ld + q] = Gs[(long)(i0 + fb.sites[l]) * ld + q];
       __syncthreads();
-      cta_gemm<T>(N, N, a, Ubuf, 1, N, Wbuf, ld, 1, Gs, ld, 1, EpiSub());
+      cta_gemm<T>(a, N, a, &fb.Tu[s][0][0], kBlock + 1, 1, Wbuf, ld, 1, MW, ld, 1, EpiStore());
+      __syncthreads();
+      path_gemm<T>(c, N, N, a, Ubuf, 1, N, MW, ld, 1, Gs, ld, 1, EpiSub());
       __syncthreads();
     }
     x.mark(kPhFlush);
@@ -433,17 +518,17 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
     if (gz) return;
     // Gt = e^{-dtau K} G (stored transposed), G = Gt e^{+dtau K}
     for (int s = 0; s < 2; ++s) {
-      cta_gemm<T>(N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
+      path_gemm<T>(c, N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
       __syncthreads();
-      cta_gemm<T>(N, N, N, Gt, 1, ld, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
+      path_gemm<T>(c, N, N, N, Gt, 1, ld, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
       __syncthreads();
     }
   } else {
     if (!gz) {
       for (int s = 0; s < 2; ++s) {
-        cta_gemm<T>(N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
+        path_gemm<T>(c, N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
         __syncthreads();
-        cta_gemm<T>(N, N, N, Gt, 1, ld, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
+        path_gemm<T>(c, N, N, N, Gt, 1, ld, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
         __syncthreads();
       }
     }
@@ -553,19 +638,22 @@ __device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, do
     householder_reflector(x, N, M, j);
     householder_apply(x, N, M + (long)j * N, x.qbeta()[j], M, j + 1, n, j);
   }
+  x.mark(kPhQR);
   PQMC_FOR_2D(col, 0, n, i, 0, N) Q[(long)col * N + i] = (i == col) ? 1.0 : 0.0;
   __syncthreads();
   for (int j = n - 1; j >= 0; --j) householder_apply(x, N, M + (long)j * N, x.qbeta()[j], Q, j, n, j);
   log_det_of(x, x.qalpha(), n, 0, logabs, sgn);
+  x.mark(kPhQRForm);
 }
 
-// Solve O_s Y_s = Y_s in place for both spins at once by LU with partial
-// pivoting (O_s: n_s x n_s row-major; Y_s: n_s x ncols_s row-major).  Warp 0
-// finds the pivots, swaps the rows and forms the multipliers; the CTA applies
-// the eliminations.  Returns log|det O_s| and sign(det O_s) to every thread.
+// Invert O_s (n_s x n_s, row-major) in place for both spins at once by
+// Gauss-Jordan elimination with partial pivoting (Golub & Van Loan, section
+// 3.2): warp s finds the pivot of spin s, swaps the rows, scales the pivot row
+// and saves the pivot column; the CTA then eliminates that column from every
+// other row; the row interchanges are undone on the columns at the end.
+// Returns log|det O_s| and sign(det O_s) to every thread.
 template <typename T>
-__device__ void lu_solve2(Cta<T>& x, const int n[2], const int ncols[2], double* O[2], double* Y[2],
-                          double logabs[2], double sgn[2]) {
+__device__ void gj_invert2(Cta<T>& x, const int n[2], double* O[2], double logabs[2], double sgn[2]) {
   Smem<T>& sh = x.sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nmax = n[0] > n[1] ? n[0] : n[1];
@@ -573,78 +661,103 @@ __device__ void lu_solve2(Cta<T>& x, const int n[2], const int ncols[2], double*
   __syncthreads();
   for (int j = 0; j < nmax; ++j) {
     if (warp < 2 && j < n[warp]) {
-      const int s = warp, ns = n[s], nc = ncols[s];
-      double* Os = O[s];
-      double* Ys = Y[s];
-      double best = -1.0;
+      const int s = warp, ns = n[s];
+      double* A = O[s];
+      double* f = x.lmul(s);
+      // pivot: largest |A_ij|, i >= j, ties to the lower row; |x| is compared
+      // through the bit pattern with the sign cleared, which orders
+      // non-negative doubles like their values
+      unsigned long long best = 0;
       int bi = j;
       for (int i = j + lane; i < ns; i += 32) {
-        const double v = fabs(Os[(long)i * ns + j]);
-        if (v > best) { best = v; bi = i; }
+        const unsigned long long v = (unsigned long long)__double_as_longlong(A[(long)i * ns + j]) & 0x7fffffffffffffffull;
+        if (v > best || bi == j && i == j) { best = v; bi = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (bi != j) {
         for (int col = lane; col < ns; col += 32) {
-          const double t = Os[(long)j * ns + col];
-          Os[(long)j * ns + col] = Os[(long)bi * ns + col];
-          Os[(long)bi * ns + col] = t;
-        }
-        for (int col = lane; col < nc; col += 32) {
-          const double t = Ys[(long)j * nc + col];
-          Ys[(long)j * nc + col] = Ys[(long)bi * nc + col];
-          Ys[(long)bi * nc + col] = t;
+          const double t = A[(long)j * ns + col];
+          A[(long)j * ns + col] = A[(long)bi * ns + col];
+          A[(long)bi * ns + col] = t;
         }
         if (lane == 0) sh.nswap[s]++;
       }
+      if (lane == 0) x.pinv(s)[j] = (double)bi;         // row interchange of step j
       __syncwarp();
-      const double pv = Os[(long)j * ns + j];
-      const double pinv = pv != 0.0 ? 1.0 / pv : 0.0;
+      const double pv = A[(long)j * ns + j];
+      const double ip = pv != 0.0 ? 1.0 / pv : 0.0;
       if (lane == 0) {
         x.pval(s)[j] = pv;
-        x.pinv(s)[j] = pinv;
         if (pv == 0.0) sh.err |= kErrStab;
       }
-      for (int i = j + 1 + lane; i < ns; i += 32) x.lmul(s)[i] = Os[(long)i * ns + j] * pinv;
+      for (int i = lane; i < ns; i += 32) f[i] = A[(long)i * ns + j];
+      __syncwarp();
+      for (int col = lane; col < ns; col += 32) A[(long)j * ns + col] = (col == j) ? ip : A[(long)j * ns + col] * ip;
     }
     __syncthreads();
     for (int s = 0; s < 2; ++s) {
       if (j >= n[s]) continue;
-      const int ns = n[s], nc = ncols[s];
-      double* Os = O[s];
-      double* Ys = Y[s];
-      const double* lm = x.lmul(s);
-      const int nt = ns - j - 1;
-      PQMC_FOR_2D(i, j + 1, ns, col, 0, nt + nc) {
-        if (col < nt)
-          Os[(long)i * ns + j + 1 + col] = fma(-lm[i], Os[(long)j * ns + j + 1 + col], Os[(long)i * ns + j + 1 + col]);
-        else
-          Ys[(long)i * nc + col - nt] = fma(-lm[i], Ys[(long)j * nc + col - nt], Ys[(long)i * nc + col - nt]);
+      const int ns = n[s];
+      double* A = O[s];
+      const double* f = x.lmul(s);
+      PQMC_FOR_2D(i, 0, ns, col, 0, ns) {
+        if (i == j) continue;
+        if (col == j) A[(long)i * ns + j] = -f[i] * A[(long)j * ns + j];
+        else A[(long)i * ns + col] = fma(-f[i], A[(long)j * ns + col], A[(long)i * ns + col]);
       }
     }
     __syncthreads();
   }
-  // back substitution, both spins
-  for (int j = nmax - 1; j >= 0; --j) {
-    for (int s = 0; s < 2; ++s) {
-      if (j >= n[s]) continue;
-      const double inv = x.pinv(s)[j];
-      for (int col = threadIdx.x; col < ncols[s]; col += blockDim.x) Y[s][(long)j * ncols[s] + col] *= inv;
+  // undo the row interchanges on the columns, last step first
+  if (warp < 2) {
+    const int s = warp, ns = n[s];
+    double* A = O[s];
+    for (int j = ns - 1; j >= 0; --j) {
+      const int p = (int)x.pinv(s)[j];
+      if (p != j)
+        for (int i = lane; i < ns; i += 32) {
+          const double t = A[(long)i * ns + j];
+          A[(long)i * ns + j] = A[(long)i * ns + p];
+          A[(long)i * ns + p] = t;
+        }
+      __syncwarp();
     }
-    __syncthreads();
-    for (int s = 0; s < 2; ++s) {
-      if (j >= n[s]) continue;
-      const int ns = n[s], nc = ncols[s];
-      PQMC_FOR_2D(i, 0, j, col, 0, nc)
-        Y[s][(long)i * nc + col] = fma(-O[s][(long)i * ns + j], Y[s][(long)j * nc + col], Y[s][(long)i * nc + col]);
-    }
-    __syncthreads();
   }
+  __syncthreads();
   for (int s = 0; s < 2; ++s) log_det_of(x, x.pval(s), n[s], sh.nswap[s], logabs[s], sgn[s]);
+}
+
+// C = A^T B for column-major A, B (K x m and K x m', ld K): FP64, 2 x 2
+// outputs per thread, so that small products still occupy every warp.
+__device__ void gemm_tn_f64(int m, int mp, int K, const double* A, const double* B, double* C, int ldc) {
+  const int tm = (m + 1) >> 1, tn = (mp + 1) >> 1;
+  for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
+    const int i0 = (t / tn) << 1, j0 = (t % tn) << 1;
+    const double* a0 = A + (long)i0 * K;
+    const double* a1 = A + (long)min(i0 + 1, m - 1) * K;
+    const double* b0 = B + (long)j0 * K;
+    const double* b1 = B + (long)min(j0 + 1, mp - 1) * K;
+    double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const double x0 = a0[k], x1 = a1[k], y0 = b0[k], y1 = b1[k];
+      c00 = fma(x0, y0, c00);
+      c01 = fma(x0, y1, c01);
+      c10 = fma(x1, y0, c10);
+      c11 = fma(x1, y1, c11);
+    }
+    C[(long)i0 * ldc + j0] = c00;
+    if (j0 + 1 < mp) C[(long)i0 * ldc + j0 + 1] = c01;
+    if (i0 + 1 < m) {
+      C[(long)(i0 + 1) * ldc + j0] = c10;
+      if (j0 + 1 < mp) C[(long)(i0 + 1) * ldc + j0 + 1] = c11;
+    }
+  }
 }
 
 __device__ void copy_block(const double* src, double* dst, int n) {
@@ -777,17 +890,15 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
   double sign_total = 1.0;
   int n[2] = {x.nsig(0), x.nsig(1)};
   double* O[2] = {x.Ob(0), x.Ob(1)};
-  double* X[2] = {x.Xb(0), x.Xb(1)};
   const double* QR[2] = {stack_block(x, c.Rst, b, 0), stack_block(x, c.Rst, b, 1)};
   const double* QL[2] = {stack_block(x, c.Lst, b, 0), stack_block(x, c.Lst, b, 1)};
-  // O_s = Q_L^T Q_R and X_s = O_s^{-1} in FP64, both spins together
-  for (int s = 0; s < 2; ++s) {
-    cta_gemm<double>(n[s], n[s], N, QL[s], N, 1, QR[s], 1, N, O[s], n[s], 1, EpiStore());
-    PQMC_FOR_2D(r, 0, n[s], q, 0, n[s]) X[s][(long)r * n[s] + q] = (r == q) ? 1.0 : 0.0;
-  }
+  // O_s = Q_L^T Q_R and its inverse in FP64, both spins together
+  for (int s = 0; s < 2; ++s) gemm_tn_f64(n[s], n[s], N, QL[s], QR[s], O[s], n[s]);
   __syncthreads();
+  x.mark(kPhOverlap);
   double la[2], sg[2];
-  lu_solve2(x, n, n, O, X, la, sg);
+  gj_invert2(x, n, O, la, sg);
+  x.mark(kPhLU);
   for (int s = 0; s < 2; ++s) {
     // Y = X Q_L^T (n x N), G_fresh = 1 - Q_R Y, in the path precision
     const T* qr = reinterpret_cast<const T*>(QR[s]);
@@ -803,7 +914,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
       ql = qlt;
       __syncthreads();
     }
-    cta_gemm<T>(n[s], N, n[s], X[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
+    cta_gemm<T>(n[s], N, n[s], O[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
     __syncthreads();
     EpiFresh<T> epi{x.G(s), ld, &dmax};
     cta_gemm<T>(N, N, n[s], qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
@@ -816,6 +927,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     sign_total *= s_tot;
     __syncthreads();
   }
+  x.mark(kPhAssemble);
   const double dm = cta_max((double)dmax, sh.red);
   if (threadIdx.x == 0) {
     const double dmax = dm;
@@ -959,7 +1071,8 @@ __device__ Cta<T> make_cta(const ChainDesc& c, unsigned char* smem_raw, size_t r
   unsigned char* dyn = smem_raw + al16(sizeof(Smem<T>));
   T* Gp = res ? reinterpret_cast<T*>(dyn) : reinterpret_cast<T*>(c.G);
   unsigned char* scr = res ? dyn + al16(2 * (size_t)c.N * c.ld * ts) : reinterpret_cast<unsigned char*>(c.scratch);
-  Cta<T> x{c, sh, seed, Gp, scr, L, res};
+  FlipBuf<T>* fb = reinterpret_cast<FlipBuf<T>*>(res ? scr + L.fb : dyn);
+  Cta<T> x{c, sh, seed, Gp, scr, L, res, fb};
   if (res) {
     const T* g = reinterpret_cast<const T*>(c.G);
     for (long e = threadIdx.x; e < 2L * c.N * c.ld; e += blockDim.x) Gp[e] = g[e];
@@ -1034,10 +1147,16 @@ size_t smem_resident_cap(int prec, int tpb) {
   return per_cta > fixed ? per_cta - fixed : 0;
 }
 
+template <typename T>
+static size_t dyn_smem(size_t res) {
+  const size_t fbb = flipbuf_bytes((int)sizeof(T));
+  return al16(sizeof(Smem<T>)) + (res > fbb ? res : fbb);
+}
+
 template <typename T, int TPB, int MINB>
 static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res, int* d_err,
                                  cudaStream_t stream) {
-  const size_t sm = al16(sizeof(Smem<T>)) + res;
+  const size_t sm = dyn_smem<T>(res);
   cudaError_t e = cudaFuncSetAttribute(init_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   init_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, chain0, seed, res, d_err);
@@ -1047,7 +1166,7 @@ static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, u
 template <typename T, int TPB, int MINB>
 static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0, int n_sweeps,
                                   int measure, size_t res, int* d_err, cudaStream_t stream) {
-  const size_t sm = al16(sizeof(Smem<T>)) + res;
+  const size_t sm = dyn_smem<T>(res);
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   sweep_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, seed, sweep0, n_sweeps, measure, res, d_err);

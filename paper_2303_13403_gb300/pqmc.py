@@ -222,10 +222,11 @@ class Context:
         _check(load().pqmc_get_stab_errors(self._h, chain, _dptr(out), C.byref(n)), self._h)
         return out[: n.value]
 
-    PHASES = ("flip", "flush", "wrap", "stack", "qr", "refresh", "measure", "total")
+    PHASES = ("flip", "flush", "wrap", "stack", "qr", "refresh", "measure", "total", "qr_form", "overlap", "lu",
+              "assemble")
 
     def phase_cycles(self, chain=0):
-        out = (C.c_longlong * 8)()
+        out = (C.c_longlong * 12)()
         _check(load().pqmc_get_phase_cycles(self._h, chain, out), self._h)
         return dict(zip(self.PHASES, list(out)))
 

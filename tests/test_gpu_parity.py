@@ -172,12 +172,12 @@ def test_fp32_stabilisation_error_distribution():
     assert np.percentile(errs, 99.9) <= 1e-4 and errs.max() < 2e-3
 
 
-@pytest.mark.parametrize("prec", [pqmc.FP64, pqmc.FP32])
+@pytest.mark.parametrize("prec", [pqmc.FP64, pqmc.FP32, pqmc.BF16X3])
 def test_mc_energy_within_3sigma_of_exact(prec):
     """64 independent chains on the 8-site cluster; the pooled estimate of E and
     docc agrees with the exact Trotterised projection (Fock space) within 3 sigma."""
     spec = SMALL
-    ctx = pqmc.Context([spec] * 64, prec=prec, seed=21, n_stab=5)
+    ctx = pqmc.Context([spec] * 64, prec=prec, seed=21, n_stab=5 if prec == pqmc.FP64 else 2)
     ctx.sweep(10, measure=False)
     ctx.sweep(60, measure=True)
     obs = ctx.measure(-1)
@@ -189,3 +189,21 @@ def test_mc_energy_within_3sigma_of_exact(prec):
     assert abs(obs["docc"] - Dx / 8) < 3 * obs["docc_err"], (obs, Dx / 8)
     assert obs["E_err"] < 0.01
     assert obs["sign"] == 1.0
+
+
+def test_bf16x3_green_and_stabilisation_error():
+    """BF16X3: the wrap and delayed-update products run as three BF16 tensor-core
+    products (about 16 significant bits); G after the FP64 stabilisation is
+    FP32-exact, the drift between stabilisations is reported per interval."""
+    spec = workloads.GUTZ_72[4.0]
+    fields = workloads.random_fields(spec, seed=3)
+    ctx = pqmc.Context([spec], prec=pqmc.BF16X3, seed=7, n_stab=2)
+    ctx.set_fields(fields)
+    ch = opq.Chain(oracle_params(spec, n_stab=2), fields=fields)
+    for s, sg in ((0, 1), (1, -1)):
+        assert np.abs(ctx.green(0, s) - ch.G[sg]).max() < 1e-5
+    batch = pqmc.Context([spec] * 32, prec=pqmc.BF16X3, seed=3, n_stab=2)
+    batch.sweep(4)
+    errs = np.concatenate([batch.stab_errors(c) for c in range(32)])
+    assert len(errs) == 32 * 4 * 21
+    assert np.median(errs) < 1e-3 and np.percentile(errs, 99) < 2e-2
