@@ -11,7 +11,7 @@ Philox fields are the whole input.
 One step = one sweep of every chain (each proposes all (Ltau+2) N fields
 once); metric = HS-field updates/s summed over chains and GPUs.
 
-  python bench.py [--gpus N --steps K --warmup W] [--prec fp32|fp64] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--prec fp32|bf16x3|fp64] [--impl reference]
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 (the slow reference program) on the host cores on a bounded sample of the
@@ -40,11 +40,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3", "fp64"])
     ap.add_argument("--chains", type=int, default=608, help="chains per GPU (4 per SM)")
     ap.add_argument("--two-theta", type=float, default=8.0)
-    ap.add_argument("--n-stab", type=int, default=0, help="0: 4 for fp32, 10 for fp64")
-    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 path timed beside (0: skip)")
+    ap.add_argument("--n-stab", type=int, default=0, help="0: 2 for fp32 and bf16x3, 10 for fp64")
+    ap.add_argument("--beside-steps", type=int, default=3, help="steps of the other precisions timed beside (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -146,27 +146,27 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def algorithmic_flops(N, n_sigma, Ltau, n_stab, acc):
-    """Per sweep per chain, both spins (see the measurement section of the design doc):
-    wrap 4 N^3 and delayed-update flush 2 acc N^3 per interaction slice per spin
-    (path precision); stack products 2 N^2 n_sigma per slice per spin, and per
-    stabilisation per spin: QR 2 n^2 (N - n/3), Q_L^T Q_R 2 n^2 N,
-    LU + solve 2/3 n^3 + 2 n^2 N, G assembly 2 N^2 n (FP64)."""
-    n = n_sigma
-    path = 2 * Ltau * (4 * N ** 3 + 2 * acc * N ** 3)
-    n_stab_pts = Ltau // n_stab + 1
-    fp64 = 2 * (Ltau * 2 * N * N * n
-                + n_stab_pts * (2 * n * n * (N - n / 3) + 2 * n * n * N + 2 / 3 * n ** 3 + 2 * n * n * N
-                                + 2 * N * N * n))
-    return path, fp64
-
-
 # ---------------------------------------------------------------- our arm
+def sweep_flops(N, n, Ltau, n_stab, acc):
+    """Algorithmic flops per sweep per chain, both spins: (path-precision, FP64).
+
+    Path precision, per interaction slice per spin: wrap 4 N^3, delayed-update
+    flush 2 acc N^3, stack slice products 2 N^2 n.  FP64, per stabilisation per
+    spin: Householder QR 2 n^2 (N - n/3), forming Q 2 n^2 (N - n/3),
+    Q_L^T Q_R 2 n^2 N, Gauss-Jordan inverse 2 n^3."""
+    path = 2 * Ltau * (4 * N ** 3 + 2 * acc * N ** 3 + 2 * N * N * n)
+    stab = (Ltau // n_stab + 1) * 2 * (4 * n * n * (N - n / 3) + 2 * n * n * N + 2 * n ** 3)
+    return path, stab
+
+
+FP64_PEAK_TFLOPS = 1.2   # measured on this pool's GB300 (FMA throughput probe; DGEMM 1.06)
+
+
 def run_ours(a):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2303_13403_gb300 import pqmc, workloads
+    from paper_2303_13403_gb300 import distributed, pqmc, workloads
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -175,8 +175,8 @@ def run_ours(a):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = {"fp32": pqmc.FP32, "fp64": pqmc.FP64}[a.prec]
-    n_stab = a.n_stab or (4 if prec != pqmc.FP64 else 10)
+    PRECS = {"fp32": pqmc.FP32, "bf16x3": pqmc.BF16X3, "fp64": pqmc.FP64}
+    NSTAB = {"fp32": 2, "bf16x3": 2, "fp64": 10}
     spec = workloads.ChainSpec(**{**WORKLOAD, "two_theta": a.two_theta})
     specs = [spec] * a.chains
     stream = torch.cuda.Stream(device=dev)
@@ -185,17 +185,19 @@ def run_ours(a):
         if world > 1:
             dist.barrier()
 
-    def timed(prec_, n_stab_, steps, warmup):
-        ctx = pqmc.Context(specs, prec=prec_, seed=1, n_stab=n_stab_, chain_offset=rank * a.chains,
+    def timed(name, n_stab_, steps, warmup, clocks=False):
+        ctx = pqmc.Context(specs, prec=PRECS[name], seed=1, n_stab=n_stab_, chain_offset=rank * a.chains,
                            max_meas=warmup + steps + 1, stream=stream.cuda_stream)
         for _ in range(warmup):
-            ctx.sweep(1, measure=True)
+            ctx.sweep(1, measure=False)
         ctx.synchronize()
         torch.cuda.synchronize()
         barrier()
-        clk = ClockSampler(local)
-        clk.start()
-        time.sleep(0.3)
+        clk = ClockSampler(local) if clocks else None
+        if clk:
+            clk.start()
+            time.sleep(0.3)
+        launches0 = ctx.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -206,29 +208,56 @@ def run_ours(a):
         ctx.synchronize()
         torch.cuda.synchronize()
         barrier()
-        clocks = clk.stop()
+        cl = clk.stop() if clk else None
         ms = e0.elapsed_time(e1)
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         obs = ctx.measure(-1)
-        launches = ctx.launch_count()
-        dims = ctx.dims(0)
+        # pooled over the chains of every rank (jackknife over chains)
+        sums = distributed.chain_sums([ctx.measurements(c, cap=steps + 1) for c in range(a.chains)])
+        if world > 1:
+            sums = distributed.gather_sums(sums)
+        pooled = distributed.pooled_estimate(sums)
+        obs["E"], obs["E_err"] = pooled["E"], pooled["E_err"]
+        errs = np.concatenate([ctx.stab_errors(c, cap=4096) for c in range(min(a.chains, 64))])
+        out = {"ms": float(t.item()), "clocks": cl, "obs": obs, "launches": ctx.launch_count() - launches0,
+               "dims": ctx.dims(0), "dG": errs}
         ctx.close()
-        return float(t.item()), clocks, obs, launches, dims
+        return out
 
-    ms, clocks, obs, launches, d = timed(prec, n_stab, a.steps, a.warmup)
-    N, Ltau = d["N"], d["Ltau"]
+    def summary(name, r, steps):
+        N, Ltau = r["dims"]["N"], r["dims"]["Ltau"]
+        props = (Ltau + 2) * N
+        ups = props * a.chains * world * steps / (r["ms"] / 1e3)
+        chain_sweeps_per_s = a.chains * world * steps / (r["ms"] / 1e3)
+        o = r["obs"]
+        # chains are independent and equilibrated: sigma(E) ~ 1/sqrt(chain-sweeps)
+        need = a.chains * world * steps * (o["E_err"] / 1e-3) ** 2 if o["E_err"] == o["E_err"] else float("nan")
+        # (sigma measured from the timed sweeps of every chain, pooled over ranks)
+        dg = r["dG"]
+        return {"value": ups, "unit": UNIT, "n_stab": NSTAB[name] if not a.n_stab else a.n_stab,
+                "ms_per_step": r["ms"] / steps, "E_per_site": o["E"], "E_err": o["E_err"], "accept": o["accept"],
+                "time_to_sigma_1e-3_s": need / chain_sweeps_per_s,
+                "dG_per_stabilisation": {"median": float(np.median(dg)), "p99": float(np.percentile(dg, 99)),
+                                         "p999": float(np.percentile(dg, 99.9)), "max": float(dg.max())}}
+
+    head = a.prec
+    n_stab = a.n_stab or NSTAB[head]
+    r = timed(head, n_stab, a.steps, a.warmup, clocks=True)
+    res = summary(head, r, a.steps)
+    N, Ltau = r["dims"]["N"], r["dims"]["Ltau"]
     props_per_chain = (Ltau + 2) * N
     updates = props_per_chain * a.chains * world * a.steps
-    value = updates / (ms / 1e3)
+    ms = r["ms"]
 
-    # FP64 path timed beside it (the plain FP64 GPU sweep the reduced paths must beat)
-    fp64 = None
-    if prec != pqmc.FP64 and a.fp64_steps > 0:
-        ms64, _, obs64, _, _ = timed(pqmc.FP64, 10, a.fp64_steps, 1)
-        fp64 = {"value": props_per_chain * a.chains * world * a.fp64_steps / (ms64 / 1e3), "unit": UNIT,
-                "n_stab": 10, "ms_per_step": ms64 / a.fp64_steps, "max_dG": obs64["max_dG"]}
+    beside = {}
+    if a.beside_steps > 0:
+        for name in PRECS:
+            if name == head:
+                continue
+            rb = timed(name, NSTAB[name], a.beside_steps, 2)
+            beside[name + "_gpu"] = summary(name, rb, a.beside_steps)
 
     # end to end through the public API with host buffers: context creation
     # (host model set-up + upload of the arena from host memory) and, every
@@ -236,7 +265,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    ctx = pqmc.Context(specs, prec=prec, seed=2, n_stab=n_stab, chain_offset=rank * a.chains,
+    ctx = pqmc.Context(specs, prec=PRECS[head], seed=2, n_stab=n_stab, chain_offset=rank * a.chains,
                        max_meas=a.steps + 1, stream=stream.cuda_stream)
     h2d = ctx.device_bytes()
     rec = np.zeros((a.chains, 5))
@@ -252,43 +281,53 @@ def run_ours(a):
     e2e_value = updates / float(t.item())
     ctx.close()
 
-    path_flops, fp64_flops = algorithmic_flops(N, N // 2, Ltau, n_stab, obs["accept"])
-    launch_s = ms / 1e3 / a.steps                     # one sweep launch per step
-    achieved = path_flops * a.chains / launch_s / 1e12
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    peak = fp32_peak_tflops(2070.0) if prec == pqmc.FP32 else 1.2
+    # roofline of the sweep kernel (one launch per step): the binding pipe is
+    # FP64 for every path (the stabilisation in the reduced paths, everything
+    # in the FP64 path)
+    path_f, stab_f = sweep_flops(N, N // 2, Ltau, n_stab, res["accept"])
+    launch_s = ms / 1e3 / a.steps
+    fp64_f = stab_f + (path_f if head == "fp64" else 0.0)
+    fp64_achieved = fp64_f * a.chains / launch_s / 1e12
+    fp32_achieved = (path_f * a.chains / launch_s / 1e12) if head != "fp64" else 0.0
+    fp32_peak = fp32_peak_tflops(2070.0)
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64"}[a.prec], "data": "synthetic",
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "fp64": "f64"}[head], "data": "synthetic",
         "config": {"workload": "gutzwiller_pqmc_honeycomb_6x6_U4_g0.6_MN0.21_2theta%g" % a.two_theta,
                    "sites": N, "slices": Ltau + 2, "chains_per_gpu": a.chains, "global_chains": a.chains * world,
-                   "n_stab": n_stab, "delay_block": 32, "precision": a.prec,
+                   "n_stab": n_stab, "delay_block": 32, "precision": head,
                    "l2": "state larger than L2 (%.0f MB of chain state per GPU vs 129 MB L2)" %
-                         (a.chains * (2 * 2 * N * N * (4 if prec != pqmc.FP64 else 8)
+                         (a.chains * (2 * 2 * N * N * (4 if head != "fp64" else 8)
                                       + 4 * (Ltau // n_stab + 1) * N * (N // 2) * 8) / 1e6),
                    "parallelism": "chains%d" % world},
-        "clocks": clocks,
-        "gpu_launches": launches,
-        "accept": obs["accept"], "max_dG": obs["max_dG"], "E_per_site": obs["E"], "E_err": obs["E_err"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "sweep_kernel", "peak_source": "FP32 FFMA 152x128x2 at 2070 MHz" if prec == pqmc.FP32
-                     else "FP64 measured 1.2 TFLOP/s (FMA probe)"},
-        "fp64_flops_per_sweep": fp64_flops * a.chains,
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "time_to_sigma_1e-3_s": res["time_to_sigma_1e-3_s"],
+        "E_per_site": res["E_per_site"], "E_err": res["E_err"], "accept": res["accept"],
+        "dG_per_stabilisation": res["dG_per_stabilisation"],
+        "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": fp64_achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sweep_kernel",
+                     "pipe": "fp64",
+                     "peak_source": "FP64 FMA throughput measured on this pool's GB300 (1.2 TFLOP/s)",
+                     "fp32_pipe": {"achieved": fp32_achieved, "peak": fp32_peak,
+                                   "frac": fp32_achieved / fp32_peak,
+                                   "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(a.steps, 1),
                 "d2h_bytes_per_step": d2h // max(a.steps, 1),
                 "note": "timed: context creation (host FP64 model build, upload of the whole device arena "
                         "from host memory, device initialisation) + per step one sweep and the device-to-host "
                         "read of every chain's new measurement; h2d is the arena upload spread over the steps"},
     }
-    if fp64:
-        result["fp64_gpu"] = fp64
+    result.update(beside)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        rate, cores, n_upd = oracle_rate(a.two_theta, n_stab, a.cpu_seconds)
+        rate, cores, n_upd = oracle_rate(a.two_theta, NSTAB["fp64"], a.cpu_seconds)
+        cs_per_s = rate / props_per_chain
+        need = a.chains * a.steps * (res["E_err"] / 1e-3) ** 2
         result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                  "sample": "%d oracle chains (one per core), ~%gs of sweeps each, %d updates" %
-                                            (cores, a.cpu_seconds, n_upd)}
+                                  "sample": "%d oracle chains (one per core, FP64, n_stab 10), ~%gs of sweeps "
+                                            "each, %d updates" % (cores, a.cpu_seconds, n_upd),
+                                  "time_to_sigma_1e-3_s": need / cs_per_s}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -300,7 +339,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_stab = a.n_stab or (4 if a.prec != "fp64" else 10)
+    n_stab = a.n_stab or 10
     seconds = max(2.0, min(10.0, 120.0 / max(a.steps + a.warmup, 1)))
     for _ in range(a.warmup):
         oracle_rate(a.two_theta, n_stab, 0.5)

@@ -152,7 +152,10 @@ pqmc_status pqmc_init_batch(int n, const pqmc_chain_spec* specs, const pqmc_opts
                             pqmc_ctx** out);
 
 /* Enqueue n_sweeps sweeps of every chain on the context's stream
- * (asynchronous). measure != 0 records one measurement per sweep and chain. */
+ * (asynchronous). measure != 0 records one measurement per sweep and chain.
+ * All chains run in one launch; the first call with a given (n_sweeps,
+ * measure) captures that launch (and the advance of the device-side sweep
+ * index) in a CUDA graph, later calls replay it. */
 pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure);
 
 /* Wait for the context's stream and report any device-side error. */
@@ -212,7 +215,8 @@ int pqmc_num_chains(const pqmc_ctx* ctx);
  * creation), or 0 for NULL. */
 size_t pqmc_device_bytes(const pqmc_ctx* ctx);
 
-/* Device kernels launched by this context so far (all entry points). */
+/* Device kernels launched by this context so far (all entry points; a sweep
+ * graph replay counts its two kernels). */
 long pqmc_launch_count(const pqmc_ctx* ctx);
 
 /* Last error message of a context (or of the last failed pqmc_init* call when

@@ -22,7 +22,8 @@ namespace pqmc {
 size_t smem_resident_cap(int prec, int tpb);
 cudaError_t launch_init(int prec, int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,
                         int* d_err, cudaStream_t stream);
-cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0,
+cudaError_t prepare_sweep(int prec, int tpb, size_t res);
+cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,
                          int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
 }  // namespace pqmc
 
@@ -56,6 +57,9 @@ struct pqmc_ctx {
   int* d_err = nullptr;
   size_t off_last = 0;                     // n_chains x kRecord latest records
   size_t res_bytes = 0;                    // shared memory offered for resident chains
+  uint32_t* d_sweep = nullptr;             // sweep index read by the sweep kernel
+  struct GraphEntry { int n_sweeps, measure; cudaGraphExec_t exec; };
+  std::vector<GraphEntry> graphs;          // captured (sweep, advance) pairs
   int tpb = 256;                           // threads per chain CTA
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -305,7 +309,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   e = cudaMalloc(&ctx->d_arena, ctx->arena_bytes);
   if (e != cudaSuccess) { pqmc_free(ctx); return fail(nullptr, PQMC_ENOMEM, std::string("device arena: ") + cudaGetErrorString(e)); }
   e = cudaMalloc(&ctx->d_desc, sizeof(ChainDesc) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 2 * sizeof(int));
+  if (e == cudaSuccess) ctx->d_sweep = reinterpret_cast<uint32_t*>(ctx->d_err + 1);
   if (e != cudaSuccess) { pqmc_free(ctx); return fail(nullptr, PQMC_ENOMEM, "device descriptors"); }
   ctx->desc.resize(n);
   for (int c = 0; c < n; ++c) {
@@ -350,7 +355,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   e = cudaMemcpyAsync(ctx->d_arena, A.data(), ctx->arena_bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->res_bytes);
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
   e = launch_init(ctx->prec, ctx->tpb, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
   ctx->launches++;
@@ -429,10 +435,30 @@ pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
   if (!ctx || n_sweeps < 0) return PQMC_EINVAL;
   if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
   if (n_sweeps == 0) return PQMC_OK;
-  cudaError_t e = launch_sweep(ctx->prec, ctx->tpb, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed, ctx->sweep_index,
-                               n_sweeps, measure, ctx->res_bytes, ctx->d_err, ctx->stream);
-  ctx->launches++;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
+  // one captured graph per (n_sweeps, measure): the sweep launch and the
+  // advance of the device-side sweep index, replayed on the context's stream
+  const int meas = measure ? 1 : 0;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : ctx->graphs)
+    if (g.n_sweeps == n_sweeps && g.measure == meas) exec = g.exec;
+  cudaError_t e = cudaSuccess;
+  if (!exec) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t el = launch_sweep(ctx->prec, ctx->tpb, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed,
+                                          ctx->d_sweep, n_sweeps, meas, ctx->res_bytes, ctx->d_err, ctx->stream);
+      e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep graph capture");
+    ctx->graphs.push_back({n_sweeps, meas, exec});
+  }
+  e = cudaGraphLaunch(exec, ctx->stream);
+  ctx->launches += 2;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep graph launch");
   ctx->sweep_index += (uint32_t)n_sweeps;
   return PQMC_OK;
 }
@@ -643,6 +669,7 @@ const char* pqmc_last_error(const pqmc_ctx* ctx) {
 void pqmc_free(pqmc_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   if (ctx->d_desc) cudaFree(ctx->d_desc);
   if (ctx->d_err) cudaFree(ctx->d_err);

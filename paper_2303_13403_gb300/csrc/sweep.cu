@@ -89,15 +89,23 @@ __device__ double cta_max(double v, double* red) {
 // 16-byte vector loads.
 
 struct EpiStore {
+  static constexpr bool kRow4 = true;   // supports 4 contiguous outputs of a row at once
   template <typename T, typename TC> __device__ void operator()(TC* C, int sci, int scj, int i, int j, T v) const {
     C[(long)i * sci + (long)j * scj] = (TC)v;
   }
+  template <typename T> __device__ void row4(T* c, const T v[4]) const { c[0] = v[0]; c[1] = v[1]; c[2] = v[2]; c[3] = v[3]; }
 };
 struct EpiSub {
+  static constexpr bool kRow4 = true;
   template <typename T, typename TC> __device__ void operator()(TC* C, int sci, int scj, int i, int j, T v) const {
     C[(long)i * sci + (long)j * scj] -= (TC)v;
   }
+  template <typename T> __device__ void row4(T* c, const T v[4]) const {
+    c[0] -= v[0]; c[1] -= v[1]; c[2] -= v[2]; c[3] -= v[3];
+  }
 };
+template <typename E, typename = void> struct HasRow4 { static constexpr bool value = false; };
+template <typename E> struct HasRow4<E, std::void_t<decltype(E::kRow4)>> { static constexpr bool value = E::kRow4; };
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
@@ -125,10 +133,16 @@ template <typename T, typename TA, typename TB, typename TC, typename Epi>
 __device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, const TB* B, int sbk, int sbj,
                          TC* C, int sci, int scj, Epi epi) {
   const int tm = (M + 3) >> 2, tn = (Nn + 3) >> 2;
-  bool vec = false;
+  bool vec = false, vec_row = false, st_row = false;
   if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
     vec = sai == 1 && sbj == 1 && vec_ok<T>((const T*)A, sak) && vec_ok<T>((const T*)B, sbk) &&
           (M % 4 == 0) && (Nn % 4 == 0);
+    // A contiguous along k (row-major): 4 x 4 blocks of A per four k-steps
+    vec_row = !vec && sak == 1 && sbj == 1 && vec_ok<T>((const T*)A, sai) && vec_ok<T>((const T*)B, sbk) &&
+              (M % 4 == 0) && (Nn % 4 == 0) && (K % 4 == 0);
+  }
+  if constexpr (std::is_same<T, TC>::value && HasRow4<Epi>::value) {
+    st_row = scj == 1 && vec_ok<T>((const T*)C, sci) && (Nn % 4 == 0);
   }
   for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
     const int i0 = (t / tn) << 2, j0 = (t % tn) << 2;
@@ -153,7 +167,26 @@ __device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, co
         }
       }
     }
-    if (!vec) {
+    if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
+      if (vec_row) {
+        const T* pa = (const T*)A + (long)i0 * sai;
+        const T* pb = (const T*)B + j0;
+        for (int k = 0; k < K; k += 4) {
+          T a[4][4], b[4][4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) Vec4<T>::load(pa + (long)r * sai + k, a[r]);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) Vec4<T>::load(pb + (long)(k + kk) * sbk, b[kk]);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r][kk], b[kk][q], acc[r][q]);
+        }
+      }
+    }
+    if (!vec && !vec_row) {
       for (int k = 0; k < K; ++k) {
         T a[4], b[4];
 #pragma unroll
@@ -164,6 +197,14 @@ __device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, co
         for (int r = 0; r < 4; ++r)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+      }
+    }
+    if constexpr (std::is_same<T, TC>::value && HasRow4<Epi>::value) {
+      if (st_row) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (i0 + r < M) epi.row4((T*)C + (long)(i0 + r) * sci + j0, acc[r]);
+        continue;
       }
     }
 #pragma unroll
@@ -516,19 +557,19 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
     }
     __syncthreads();
     if (gz) return;
-    // Gt = e^{-dtau K} G (stored transposed), G = Gt e^{+dtau K}
+    // Gt = e^{-dtau K} G, G = Gt e^{+dtau K}
     for (int s = 0; s < 2; ++s) {
-      path_gemm<T>(c, N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
+      path_gemm<T>(c, N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
       __syncthreads();
-      path_gemm<T>(c, N, N, N, Gt, 1, ld, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
+      path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
       __syncthreads();
     }
   } else {
     if (!gz) {
       for (int s = 0; s < 2; ++s) {
-        path_gemm<T>(c, N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, 1, ld, EpiStore());
+        path_gemm<T>(c, N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
         __syncthreads();
-        path_gemm<T>(c, N, N, N, Gt, 1, ld, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
+        path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
         __syncthreads();
       }
     }
@@ -1109,10 +1150,12 @@ __global__ void __launch_bounds__(TPB, MINB) init_kernel(const ChainDesc* chains
 }
 
 template <typename T, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) sweep_kernel(const ChainDesc* chains, uint64_t seed, uint32_t sweep0,
-                                                       int n_sweeps, int do_measure, size_t res_bytes, int* err) {
+__global__ void __launch_bounds__(TPB, MINB) sweep_kernel(const ChainDesc* chains, uint64_t seed,
+                                                       const uint32_t* sweep_ctr, int n_sweeps, int do_measure,
+                                                       size_t res_bytes, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (chains[blockIdx.x].st->err) return;
+  const uint32_t sweep0 = *sweep_ctr;
   Cta<T> x = make_cta<T>(chains[blockIdx.x], smem_raw, res_bytes, seed);
   Smem<T>& sh = x.sh;
   load_state(x);
@@ -1163,13 +1206,23 @@ static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, u
   return cudaGetLastError();
 }
 
+// The sweep index lives in device memory (sweep_ctr) and is advanced by a
+// one-thread kernel after each sweep launch, so that the pair can be captured
+// once in a CUDA graph and replayed.
+__global__ void advance_sweep_kernel(uint32_t* sweep_ctr, int n) { *sweep_ctr += (uint32_t)n; }
+
 template <typename T, int TPB, int MINB>
-static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0, int n_sweeps,
+static cudaError_t prepare_sweep_t(size_t res) {
+  return cudaFuncSetAttribute(sweep_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dyn_smem<T>(res));
+}
+
+template <typename T, int TPB, int MINB>
+static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr, int n_sweeps,
                                   int measure, size_t res, int* d_err, cudaStream_t stream) {
-  const size_t sm = dyn_smem<T>(res);
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  sweep_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, seed, sweep0, n_sweeps, measure, res, d_err);
+  sweep_kernel<T, TPB, MINB><<<n, TPB, dyn_smem<T>(res), stream>>>(d_chains, seed, sweep_ctr, n_sweeps, measure, res,
+                                                                   d_err);
+  advance_sweep_kernel<<<1, 1, 0, stream>>>(sweep_ctr, n_sweeps);
   return cudaGetLastError();
 }
 
@@ -1190,9 +1243,11 @@ cudaError_t launch_init(int prec, int tpb, const ChainDesc* d_chains, int chain0
   PQMC_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream);
 }
 
-cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t sweep0,
+cudaError_t prepare_sweep(int prec, int tpb, size_t res) { PQMC_DISPATCH(prepare_sweep_t, res); }
+
+cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,
                          int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {
-  PQMC_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep0, n_sweeps, measure, res, d_err, stream);
+  PQMC_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
 }
 
 // --------------------------------------------------------------------------

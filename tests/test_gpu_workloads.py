@@ -1,0 +1,83 @@
+"""The larger workloads through the C-ABI: uneven batched lattices of the
+variational scan (72/162/288 sites), the 648-site single chain, and the doped
+square lattice with signful weights."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import pqmc as opq
+from paper_2303_13403_gb300 import pqmc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_params(spec, **kw):
+    base = dict(kind=spec.kind, Lx=spec.Lx, Ly=spec.Ly, t=spec.t, tp=spec.tp, U=spec.U, dtau=spec.dtau,
+                two_theta=spec.two_theta, g=spec.g, M_N=spec.M_N, n_up=spec.n_up, n_dn=spec.n_dn,
+                tiebreak=spec.tiebreak)
+    base.update(kw)
+    return opq.Params(**base)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    torch.cuda.set_device(0)
+    pqmc.load()
+
+
+def test_uneven_batch_fixed_fields_parity():
+    """One chain of each size of the batched (g, M_N) scan in one context; FP64
+    G after initialisation on fixed fields equals the oracle to 1e-10."""
+    by_size = {}
+    for sp in workloads.variational_grid(8.0):
+        by_size.setdefault(sp.n_sites, sp)
+    specs = [by_size[72], by_size[162], by_size[288]]
+    ctx = pqmc.Context(specs, prec=pqmc.FP64, seed=3, n_stab=10)
+    for c, sp in enumerate(specs):
+        f = workloads.random_fields(sp, seed=40 + c)
+        ctx.set_fields(f, chain=c)
+        ch = opq.Chain(oracle_params(sp, n_stab=10), fields=f)
+        for s, sg in ((0, 1), (1, -1)):
+            G = ctx.green(c, s)
+            assert np.abs(G - ch.G[sg]).max() / np.abs(ch.G[sg]).max() < 1e-10, (sp.n_sites, s)
+
+
+def test_uneven_batch_sweeps_all_sizes_fp32():
+    by_size = {}
+    for sp in workloads.variational_grid(8.0):
+        by_size.setdefault(sp.n_sites, sp)
+    specs = [by_size[72], by_size[162], by_size[288]] * 2
+    ctx = pqmc.Context(specs, prec=pqmc.FP32, seed=5, n_stab=4)
+    ctx.sweep(2)
+    for c in range(len(specs)):
+        rec = ctx.measurements(c)
+        assert len(rec) == 2 and np.all(np.isfinite(rec)) and np.all(rec[:, 0] == 1.0)
+        assert -1.2 < rec[:, 1].mean() < -0.5
+        assert ctx.stab_errors(c).max() < 5e-2
+
+
+def test_large_single_chain_648_sites():
+    """The 648-site chain (200 slices, n_stab 10) in FP32: one sweep, finite
+    records, stabilisation errors reported, sign +1 at half filling."""
+    spec = workloads.GUTZ_648
+    ctx = pqmc.Context([spec], prec=pqmc.FP32, seed=1, n_stab=10)
+    ctx.sweep(1)
+    rec = ctx.measurements(0)
+    assert len(rec) == 1 and np.all(np.isfinite(rec)) and rec[0, 0] == 1.0
+    assert -1.0 < rec[0, 1] < -0.5
+    errs = ctx.stab_errors(0)
+    assert len(errs) == 21 and np.all(np.isfinite(errs))
+
+
+def test_doped_square_signs_consistent():
+    """Doped t-t' lattice (28 up + 28 down on 64 sites): the weight sign from
+    the stabilised stacks equals the running product of sgn(R) in every record."""
+    spec = replace(workloads.DOPED_64[0.6], two_theta=4.0)
+    ctx = pqmc.Context([spec] * 16, prec=pqmc.FP64, seed=9, n_stab=10)
+    ctx.sweep(4)
+    for c in range(16):
+        rec = ctx.measurements(c)
+        assert set(np.unique(rec[:, 0])) <= {-1.0, 1.0}
+        assert np.array_equal(rec[:, 0], rec[:, 4])
