@@ -120,6 +120,8 @@ typedef struct {
     int cta_threads;        /* threads of the CTA that runs one chain: 64, 128 or 256; 0 picks
                                64 for FP64 and 128 otherwise. Smaller CTAs put more chains
                                on one SM (FP64: 256/cta_threads per SM, others twice that) */
+    int dense_chains;       /* reduced paths only: kernels built for twice as many chains per SM
+                               (fewer registers per thread); needs cta_threads 64 or 128 */
 } pqmc_opts;
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
@@ -199,10 +201,11 @@ pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);
 pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n);
 
 /* SM clock cycles one chain's CTA has spent, as seen by its thread 0, in
- * each phase of its sweeps so far: out[0..11] = (flip decisions,
+ * each phase of its sweeps so far: out[0..14] = (flip decisions,
  * delayed-update flushes, slice wrapping, stack slice products, QR
  * factorisation, rest of the G refresh, measurement, total, forming Q,
- * Q_L^T Q_R, its LU inverse, G assembly). */
+ * Q_L^T Q_R, its inverse, G assembly; and inside the inverse: pivot steps,
+ * eliminations, column restore and log-determinant). */
 pqmc_status pqmc_get_phase_cycles(pqmc_ctx* ctx, int chain, long long* out);
 
 /* Sizes of one chain: out[0..5] = (N, N_up, N_dn, Ltau, n_stab, delay_k). */

@@ -19,12 +19,12 @@
 #include "philox.cuh"
 
 namespace pqmc {
-size_t smem_resident_cap(int prec, int tpb);
-cudaError_t launch_init(int prec, int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,
-                        int* d_err, cudaStream_t stream);
-cudaError_t prepare_sweep(int prec, int tpb, size_t res);
-cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,
-                         int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
+size_t smem_resident_cap(int prec, int tpb, int boost);
+cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
+                        size_t res, int* d_err, cudaStream_t stream);
+cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res);
+cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains, int n, uint64_t seed,
+                         uint32_t* sweep_ctr, int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
 }  // namespace pqmc
 
 using namespace pqmc;
@@ -61,6 +61,7 @@ struct pqmc_ctx {
   struct GraphEntry { int n_sweeps, measure; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;          // captured (sweep, advance) pairs
   int tpb = 256;                           // threads per chain CTA
+  int boost = 0;                           // 1: reduced-path kernels built for twice the CTAs per SM
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   uint32_t sweep_index = 0;
@@ -164,6 +165,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (o.accept_log < 0) return fail(nullptr, PQMC_EINVAL, "accept_log < 0");
   if (o.cta_threads != 0 && o.cta_threads != 64 && o.cta_threads != 128 && o.cta_threads != 256)
     return fail(nullptr, PQMC_EINVAL, "cta_threads must be 0, 64, 128 or 256");
+  if (o.dense_chains && o.prec != PQMC_FP64 && o.cta_threads == 256)
+    return fail(nullptr, PQMC_EINVAL, "dense_chains needs cta_threads 64 or 128");
   for (int c = 0; c < n; ++c) {
     std::string why;
     if (check_spec(specs[c], o.n_stab, why) != PQMC_OK) return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
@@ -249,7 +252,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   // chains of 64 threads per SM, the reduced paths 4 chains of 128 threads
   ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : 128);
   {
-    const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb);
+    ctx->boost = (ctx->prec != PQMC_FP64 && o.dense_chains) ? 1 : 0;
+    const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb, ctx->boost);
     for (const HostChain& h : ctx->chains) {
       const size_t r = resident_bytes(h.N, h.ld, h.nmax, (int)ctx->tsize);
       if (r <= cap && r > ctx->res_bytes) ctx->res_bytes = r;
@@ -356,9 +360,9 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int), ctx->stream);
-  if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->res_bytes);
+  if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->res_bytes);
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
-  e = launch_init(ctx->prec, ctx->tpb, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
+  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "init launch"); }
   pqmc_status st = sync_check(ctx);
@@ -446,7 +450,7 @@ pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      const cudaError_t el = launch_sweep(ctx->prec, ctx->tpb, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed,
+      const cudaError_t el = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed,
                                           ctx->d_sweep, n_sweeps, meas, ctx->res_bytes, ctx->d_err, ctx->stream);
       e = cudaStreamEndCapture(ctx->stream, &graph);
       if (e == cudaSuccess) e = el;
@@ -563,7 +567,7 @@ pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
-  e = launch_init(ctx->prec, ctx->tpb, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
+  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "init launch");
   return sync_check(ctx);

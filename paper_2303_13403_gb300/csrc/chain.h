@@ -16,7 +16,7 @@ constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
 // phases timed with clock64() by thread 0 of each chain CTA
 enum : int {
   kPhFlip = 0, kPhFlush, kPhWrap, kPhStack, kPhQR, kPhRefresh, kPhMeasure, kPhTotal,
-  kPhQRForm, kPhOverlap, kPhLU, kPhAssemble, kPhases
+  kPhQRForm, kPhOverlap, kPhLU, kPhAssemble, kPhGJPivot, kPhGJElim, kPhGJTail, kPhases
 };
 
 // error bits written by the kernels
@@ -72,6 +72,7 @@ struct ChainDesc {
   long long acc_cap;
   ChainState* st;
 };
+static_assert(sizeof(ChainDesc) % sizeof(int) == 0, "descriptor copied word by word");
 
 }  // namespace pqmc
 

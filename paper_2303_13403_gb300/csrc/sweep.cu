@@ -313,6 +313,7 @@ struct FlipBuf {
 
 template <typename T>
 struct Smem {
+  ChainDesc desc;                   // this chain's descriptor, copied in at launch
   double red[32];                   // reduction scratch
   double vtab[2][2][2];             // e^{sigma kappa s}: [Gutzwiller?][spin][s = -1?]
   T vt[2][2][2];                    // the same in the path precision
@@ -640,13 +641,24 @@ __device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta
   }
   __syncthreads();
   for (int col = c0 + threadIdx.x; col < c1; col += blockDim.x) {
-    double d = 0.0;
+    const int nm = x.c.nmax;
+    double q[kQRParts];
 #pragma unroll
-    for (int p = 0; p < kQRParts; ++p) d += part[p * x.c.nmax + col];
-    w[col] = d * beta;
+    for (int p = 0; p < kQRParts; ++p) q[p] = part[p * nm + col];
+#pragma unroll
+    for (int h = kQRParts / 2; h > 0; h >>= 1)
+#pragma unroll
+      for (int p = 0; p < h; ++p) q[p] += q[p + h];
+    w[col] = q[0] * beta;
   }
   __syncthreads();
-  PQMC_FOR_2D(col, c0, c1, i, j, N) A[(long)col * N + i] = fma(-v[i], w[col], A[(long)col * N + i]);
+  {
+    const int rows = N - j, total = rows * (c1 - c0);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int cl = e / rows, i = j + (e - cl * rows), col = c0 + cl;
+      A[(long)col * N + i] = fma(-v[i], w[col], A[(long)col * N + i]);
+    }
+  }
   __syncthreads();
 }
 
@@ -741,18 +753,26 @@ __device__ void gj_invert2(Cta<T>& x, const int n[2], double* O[2], double logab
       for (int col = lane; col < ns; col += 32) A[(long)j * ns + col] = (col == j) ? ip : A[(long)j * ns + col] * ip;
     }
     __syncthreads();
-    for (int s = 0; s < 2; ++s) {
-      if (j >= n[s]) continue;
-      const int ns = n[s];
-      double* A = O[s];
-      const double* f = x.lmul(s);
-      PQMC_FOR_2D(i, 0, ns, col, 0, ns) {
-        if (i == j) continue;
-        if (col == j) A[(long)i * ns + j] = -f[i] * A[(long)j * ns + j];
-        else A[(long)i * ns + col] = fma(-f[i], A[(long)j * ns + col], A[(long)i * ns + col]);
+    x.mark(kPhGJPivot);
+    // eliminate column j from every other row of both spins: one FMA per
+    // element over a flat index (full warps on the FP64 pipe); the pivot
+    // column takes -f_i / pivot through the same FMA with a zero addend
+    {
+      const int e0 = j < n[0] ? n[0] * n[0] : 0;
+      const int e1 = j < n[1] ? n[1] * n[1] : 0;
+      for (int e = threadIdx.x; e < e0 + e1; e += blockDim.x) {
+        const int s = e < e0 ? 0 : 1;
+        const int ns = n[s], loc = e - (s ? e0 : 0);
+        const int i = loc / ns, col = loc - i * ns;
+        double* A = O[s];
+        const double fi = x.lmul(s)[i];
+        const double add = col == j ? 0.0 : A[(long)i * ns + col];
+        const double r = fma(-fi, A[(long)j * ns + col], add);
+        if (i != j) A[(long)i * ns + col] = r;
       }
     }
     __syncthreads();
+    x.mark(kPhGJElim);
   }
   // undo the row interchanges on the columns, last step first
   if (warp < 2) {
@@ -771,6 +791,7 @@ __device__ void gj_invert2(Cta<T>& x, const int n[2], double* O[2], double logab
   }
   __syncthreads();
   for (int s = 0; s < 2; ++s) log_det_of(x, x.pval(s), n[s], sh.nswap[s], logabs[s], sgn[s]);
+  x.mark(kPhGJTail);
 }
 
 // C = A^T B for column-major A, B (K x m and K x m', ld K): FP64, 2 x 2
@@ -1104,8 +1125,17 @@ __device__ void store_state(Cta<T>& x, int* err) {
 // Place G and the scratch: in shared memory after the fixed part when the
 // chain's footprint fits in res_bytes (G is copied in), else in global memory.
 template <typename T>
-__device__ Cta<T> make_cta(const ChainDesc& c, unsigned char* smem_raw, size_t res_bytes, uint64_t seed) {
+__device__ Cta<T> make_cta(const ChainDesc& cg, unsigned char* smem_raw, size_t res_bytes, uint64_t seed) {
   Smem<T>& sh = *reinterpret_cast<Smem<T>*>(smem_raw);
+  // the descriptor is read all through the sweep: keep a shared-memory copy
+  {
+    const int words = (int)(sizeof(ChainDesc) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(&cg);
+    int* dst = reinterpret_cast<int*>(&sh.desc);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+  }
+  const ChainDesc& c = sh.desc;
   const int ts = (int)sizeof(T);
   const ScratchLayout L = scratch_layout(c.N, c.ld, c.nmax, ts);
   const bool res = resident_bytes(c.N, c.ld, c.nmax, ts) <= res_bytes;
@@ -1180,12 +1210,12 @@ size_t smem_fixed(int prec) { return prec == 0 ? al16(sizeof(Smem<double>)) : al
 // CTAs per SM a launch is built for: the reduced paths pack twice as many
 // chains per SM as the FP64 path (their FP32 work and the FP64 stabilisation of
 // different chains overlap); smaller CTAs pack more chains.
-int ctas_per_sm(int prec, int tpb) { return (256 / tpb) * (prec == 0 ? 1 : 2); }
+int ctas_per_sm(int prec, int tpb, int boost) { return (256 / tpb) * (prec == 0 ? 1 : 2) * (boost ? 2 : 1); }
 
 // Largest resident footprint a launch offers per chain.
-size_t smem_resident_cap(int prec, int tpb) {
+size_t smem_resident_cap(int prec, int tpb, int boost) {
   const size_t per_sm = 233472, reserve = 1024;
-  const size_t per_cta = per_sm / ctas_per_sm(prec, tpb) - reserve;
+  const size_t per_cta = per_sm / ctas_per_sm(prec, tpb, boost) - reserve;
   const size_t fixed = smem_fixed(prec);
   return per_cta > fixed ? per_cta - fixed : 0;
 }
@@ -1233,20 +1263,24 @@ static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t see
       if (tpb == 128) return CALL<double, 128, 2>(__VA_ARGS__);                         \
       return CALL<double, 256, 1>(__VA_ARGS__);                                         \
     }                                                                                   \
+    if (boost) {                                                                        \
+      if (tpb == 64) return CALL<float, 64, 16>(__VA_ARGS__);                           \
+      return CALL<float, 128, 8>(__VA_ARGS__);                                          \
+    }                                                                                   \
     if (tpb == 64) return CALL<float, 64, 8>(__VA_ARGS__);                              \
     if (tpb == 128) return CALL<float, 128, 4>(__VA_ARGS__);                            \
     return CALL<float, 256, 2>(__VA_ARGS__);                                            \
   } while (0)
 
-cudaError_t launch_init(int prec, int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,
-                        int* d_err, cudaStream_t stream) {
+cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
+                        size_t res, int* d_err, cudaStream_t stream) {
   PQMC_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream);
 }
 
-cudaError_t prepare_sweep(int prec, int tpb, size_t res) { PQMC_DISPATCH(prepare_sweep_t, res); }
+cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res) { PQMC_DISPATCH(prepare_sweep_t, res); }
 
-cudaError_t launch_sweep(int prec, int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,
-                         int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {
+cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains, int n, uint64_t seed,
+                         uint32_t* sweep_ctr, int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {
   PQMC_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
 }
 
@@ -1418,7 +1452,7 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
   cudaStream_t st_ = static_cast<cudaStream_t>(stream);
   e = cudaMemcpyAsync(base, h.data(), upload, cudaMemcpyHostToDevice, st_);
   if (e == cudaSuccess) {
-    const size_t cap = smem_resident_cap(0, 256);
+    const size_t cap = smem_resident_cap(0, 256, 0);
     const size_t rb = resident_bytes(N, ld, nmax, 8);
     e = launch_init_t<double, 256, 1>(reinterpret_cast<const ChainDesc*>(base + o_desc), 0, 1, 0,
                                       rb <= cap ? rb : 0, reinterpret_cast<int*>(base + o_err), st_);

@@ -36,7 +36,7 @@ class ChainSpec(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("n_stab", C.c_int), ("delay_k", C.c_int), ("prec", C.c_int), ("seed", C.c_uint64),
                 ("n_chains", C.c_int), ("chain_offset", C.c_int), ("accept_log", C.c_int),
-                ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int)]
+                ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int), ("dense_chains", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -130,12 +130,12 @@ class Context:
     """One libpqmc context: a batch of chains on the GPU."""
 
     def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=0, chain_offset=0, accept_log=0,
-                 max_meas=0, stream=None, cta_threads=0):
+                 max_meas=0, stream=None, cta_threads=0, dense_chains=0):
         lib = load()
         specs = list(specs)
         arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
         opts = Opts(n_stab, delay_k, prec, seed, len(specs), chain_offset, accept_log, max_meas,
-                    C.c_void_p(stream) if stream else None, cta_threads)
+                    C.c_void_p(stream) if stream else None, cta_threads, dense_chains)
         h = C.c_void_p()
         _check(lib.pqmc_init_batch(len(specs), arr, C.byref(opts), C.byref(h)))
         self._h = h
@@ -223,10 +223,10 @@ class Context:
         return out[: n.value]
 
     PHASES = ("flip", "flush", "wrap", "stack", "qr", "refresh", "measure", "total", "qr_form", "overlap", "lu",
-              "assemble")
+              "assemble", "gj_pivot", "gj_elim", "gj_tail")
 
     def phase_cycles(self, chain=0):
-        out = (C.c_longlong * 12)()
+        out = (C.c_longlong * 15)()
         _check(load().pqmc_get_phase_cycles(self._h, chain, out), self._h)
         return dict(zip(self.PHASES, list(out)))
 
