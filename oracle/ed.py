@@ -101,8 +101,29 @@ class Cluster:
         return (float(np.sum(L * self.apply_H(R))) / norm,
                 float(np.sum(L * self.D * R)) / norm)
 
+    def s_afm(self, L, R, eps):
+        """<L|S|R>/<L|R> for S = (1/N^2) (sum_i eps_i S^z_i)^2, S^z_i = (n_up - n_dn)/2.
+
+        S is diagonal in the occupation basis: a basis state with up set a and
+        down set b has sum_i eps_i S^z_i = (sum_{i in a} eps_i - sum_{i in b} eps_i)/2.
+        """
+        def stagger(states):
+            return np.array([sum(eps[i] for i in range(self.N) if (st >> i) & 1) for st in states])
+        mz = 0.5 * (stagger(self.sup)[:, None] - stagger(self.sdn)[None, :])
+        return float(np.sum(L * mz * mz * R)) / float(np.sum(L * R)) / (self.N * self.N)
+
     def trotter_projection(self, P_up, P_dn, g, dtau, Ltau):
         """Exact Trotterised estimate of E and D at the middle slice."""
+        return self.energy_docc(*self.trotter_states(P_up, P_dn, g, dtau, Ltau))
+
+    def trotter_observables(self, P_up, P_dn, g, dtau, Ltau, eps):
+        """(E, D, S_AFM) of the exact Trotterised projection at the middle slice."""
+        L, R = self.trotter_states(P_up, P_dn, g, dtau, Ltau)
+        E, D = self.energy_docc(L, R)
+        return E, D, self.s_afm(L, R, eps)
+
+    def trotter_states(self, P_up, P_dn, g, dtau, Ltau):
+        """Bra and ket at the middle slice (shapes dim_up x dim_dn)."""
         def expm_sym(M, x):
             w, v = np.linalg.eigh(M)
             return (v * np.exp(x * w)) @ v.T
@@ -116,4 +137,4 @@ class Cluster:
         for _ in range(Ltau // 2):
             R = Eup @ (eV * R) @ Edn.T          # e^{-dtau K} e^{-dtau U D} on the ket
             L = eV * (Eup @ L @ Edn.T)        # transpose of the same product, bra side
-        return self.energy_docc(L, R)
+        return L, R

@@ -20,6 +20,14 @@ def all_fields(n_fields):
 
 
 def enumerate_estimator(params):
+    """(E, docc, average sign) of the exact field sum."""
+    r = enumerate_observables(params)
+    return r["E"], r["docc"], r["sign"]
+
+
+def enumerate_observables(params):
+    """Exact field sum of E, docc and S_AFM (all per the Wick estimates of
+    ``pqmc.Chain.measure``) and the average sign, as a dict."""
     m = pqmc.Model(params)
     N, Lt = m.N, m.Ltau
     n_fields = (Lt + 2) * N
@@ -48,5 +56,11 @@ def enumerate_estimator(params):
     dg = {sg: np.diagonal(G[sg], axis1=1, axis2=2) for sg in (+1, -1)}
     docc = np.sum((1 - dg[+1]) * (1 - dg[-1]), axis=1)
     E = ekin + params.U * docc
-    return (float(np.sum(W * E) / np.sum(W)), float(np.sum(W * docc) / np.sum(W)),
-            float(np.sum(W) / np.sum(np.abs(W))))
+    # staggered S^z structure factor: (stagger^2 + same-spin exchange)/(4 N^2)
+    stag = np.einsum("i,ci->c", m.eps, dg[-1] - dg[+1])
+    exch = sum(np.einsum("i,j,cji,cij->c", m.eps, m.eps, np.eye(N)[None] - G[sg], G[sg])
+               for sg in (+1, -1))
+    S = (stag ** 2 + exch) / (4.0 * N * N)
+    tot = np.sum(W)
+    return {"E": float(np.sum(W * E) / tot), "docc": float(np.sum(W * docc) / tot),
+            "s_afm": float(np.sum(W * S) / tot), "sign": float(tot / np.sum(np.abs(W)))}

@@ -166,6 +166,7 @@ class Measurement:
     energy: float        # <H> per site for Eq. (2), this configuration
     kinetic: float       # kinetic energy per site
     docc: float          # double occupancy per site
+    s_afm: float = 0.0   # staggered S^z structure factor, see Chain.measure
 
 
 @dataclass
@@ -394,9 +395,25 @@ class Chain:
         for i in range(N):
             docc += (1.0 - self.G[+1][i, i]) * (1.0 - self.G[-1][i, i])
         energy = ekin + self.p.U * docc
+        # AFM structure factor (z component, the reading taken for the
+        # undefined supplement): S = (1/N^2) sum_ij eps_i eps_j <S^z_i S^z_j>,
+        # S^z_i = (n_i,up - n_i,dn)/2.  The spins are independent at fixed
+        # fields, so Wick's theorem per spin gives
+        #   <n_i,s n_j,s'> = n_i,s n_j,s' + [s = s'] <c^+_i c_j>_s <c_i c^+_j>_s,
+        # with <c_i c^+_j> = G_ij and <c^+_i c_j> = delta_ij - G_ji.
+        stag = 0.0
+        for i in range(N):
+            stag += m.eps[i] * (self.G[-1][i, i] - self.G[+1][i, i])   # eps_i (n_up - n_dn)
+        exch = 0.0
+        for sg in (+1, -1):
+            G = self.G[sg]
+            for i in range(N):
+                for j in range(N):
+                    exch += m.eps[i] * m.eps[j] * ((1.0 if i == j else 0.0) - G[j, i]) * G[i, j]
+        s_afm = (stag * stag + exch) / (4.0 * N * N)
         self.measurements.append(Measurement(
             self.sweep_index, self.sign_stack, self.sign_running,
-            energy / N, ekin / N, docc / N))
+            energy / N, ekin / N, docc / N, s_afm))
 
     def is_stab_point(self, tau):
         return 0 <= tau <= self.m.Ltau and tau % self.p.n_stab == 0

@@ -364,3 +364,102 @@ def test_mc_energy_within_3sigma_of_exact_doped_square():
     assert abs(D - Dx) < 3 * dD
     signs = np.array([x.sign for x in ch.measurements])
     assert np.all(signs == np.array([x.sign_running for x in ch.measurements]))
+
+
+# ------------------------------------------------- AFM structure factor (f3)
+@pytest.mark.parametrize("case", ["honeycomb", "doped_vmc", "negative_weights"])
+def test_s_afm_enumeration_equals_fock_space(case):
+    """The Wick form of S_AFM = (1/N^2) sum_ij eps_i eps_j <S^z_i S^z_j>
+    (stagger squared plus same-spin exchange) summed over all fields equals
+    the diagonal Fock-space operator (sum_i eps_i S^z_i)^2 / N^2 applied to
+    the exact Trotterised bra and ket."""
+    if case == "honeycomb":
+        p = small_params()
+    elif case == "doped_vmc":
+        p = pqmc.Params(kind=lattice.SQUARE, Lx=2, Ly=4, tp=-0.2, U=4.0, dtau=0.1,
+                        two_theta=0.0, g=0.5, M_N=0.1, n_up=3, n_dn=3, n_stab=1)
+    else:
+        p = small_params(U=8.0, dtau=0.2, two_theta=0.4, g=0.5, M_N=0.1, n_up=1, n_dn=2)
+    m = pqmc.Model(p)
+    r = hs_enum.enumerate_observables(p)
+    c = ed.Cluster(m.K, m.n_sigma[1], m.n_sigma[-1], p.U)
+    Ex, Dx, Sx = c.trotter_observables(m.P[1], m.P[-1], p.g, p.dtau, m.Ltau, m.eps)
+    assert abs(r["E"] - Ex) < 1e-11 and abs(r["docc"] - Dx) < 1e-11
+    assert abs(r["s_afm"] - Sx) < 1e-12
+    assert 0.0 < Sx <= 0.25 + 1e-12
+
+
+def test_s_afm_classical_neel_limit():
+    """M_N >> t at g = 0, Theta = 0: the trial is the classical Neel state
+    (A sites up, B sites down), whose staggered moment is N/2, so
+    S_AFM = (N/2)^2 / N^2 = 1/4 up to O((t/M_N)^2)."""
+    for kind, Lx, Ly in ((lattice.HONEYCOMB, 2, 2), (lattice.SQUARE, 4, 2)):
+        p = pqmc.Params(kind=kind, Lx=Lx, Ly=Ly, U=4.0, dtau=0.1, two_theta=0.0,
+                        g=0.0, M_N=1e5, n_stab=1, seed=1)
+        ch = pqmc.Chain(p).run(0, 2)
+        for x in ch.measurements:
+            assert abs(x.s_afm - 0.25) < 1e-8
+
+
+def test_s_afm_free_fermions_closed_form():
+    """U = 0, g = 0, free Fermi-sea trial: G is the projector of the filled
+    orbitals, G = 1 - Pi with Pi the projector on the N_s lowest eigenvectors
+    of K.  With n_i = 1/2 on a half-filled bipartite lattice the stagger term
+    vanishes, <c^+_i c_j> <c_i c^+_j> = Pi_ij (delta_ij - Pi_ij), and
+        S_AFM = 2 (N_s - sum_ij eps_i eps_j Pi_ij^2) / (4 N^2).
+    Pi comes from numpy's eigh of K, not from the trial builder; the trial's
+    Neel tie-break (M_N = 1e-4) shifts S_AFM by far less than 1e-8."""
+    p = pqmc.Params(Lx=2, Ly=2, U=0.0, g=0.0, M_N=0.0, dtau=0.1, two_theta=1.0, n_stab=5, seed=2)
+    ch = pqmc.Chain(p).run(0, 2)
+    m = ch.m
+    w, v = np.linalg.eigh(m.K)
+    ns = m.N // 2
+    assert w[ns] - w[ns - 1] > 0.5                      # closed shell
+    Pi = v[:, :ns] @ v[:, :ns].T
+    want = 2.0 * (ns - np.sum(np.outer(m.eps, m.eps) * Pi * Pi)) / (4.0 * m.N ** 2)
+    for x in ch.measurements:
+        assert abs(x.s_afm - want) < 1e-8
+
+
+def test_mc_s_afm_within_3sigma_of_exact():
+    p = pqmc.Params(Lx=2, Ly=2, U=4.0, g=0.6, M_N=0.21, dtau=0.1, two_theta=2.0, n_stab=5, seed=11)
+    ch = pqmc.Chain(p).run(10, 400)
+    ms = ch.measurements
+    S, dS = pqmc.estimate([x.s_afm for x in ms], [x.sign for x in ms])
+    m = ch.m
+    c = ed.Cluster(m.K, 4, 4, p.U)
+    _, _, Sx = c.trotter_observables(m.P[1], m.P[-1], p.g, p.dtau, m.Ltau, m.eps)
+    assert abs(S - Sx) < 3 * dS and dS < 0.01
+
+
+def test_s_afm_fixed_fields_equals_fock_space():
+    """One field configuration at Theta > 0 (G not symmetric): the sweep's
+    Wick estimate of S_AFM on G(Ltau/2) equals <L|S|R>/<L|R> with |R> and
+    <L| the Slater determinants of B_R and B_L of each spin, built in Fock
+    space.  Pins the index order of the exchange term."""
+    p = small_params(two_theta=0.4, Lx=2, Ly=1)
+    m = pqmc.Model(p)
+    rng = np.random.default_rng(4)
+    fields = rng.choice(np.array([-1, 1], dtype=np.int8), size=(m.Ltau + 2, m.N))
+    ch = pqmc.Chain(p, fields=fields.copy())
+    t = m.Ltau // 2
+    ch.G = {sg: pqmc.green_definition(m, fields, t, sg) for sg in (+1, -1)}
+    ch.measure()
+    got = ch.measurements[-1].s_afm
+    c = ed.Cluster(m.K, m.n_sigma[1], m.n_sigma[-1], p.U)
+    vec = {}
+    for sg in (+1, -1):
+        R = m.P[sg].copy()
+        for tt in range(0, t + 1):
+            R = m.B(tt, sg, fields[tt]) @ R
+        Lt = m.P[sg].copy()
+        for tt in range(m.Ltau + 1, t, -1):
+            Lt = m.B(tt, sg, fields[tt]).T @ Lt
+        states = c.sup if sg == 1 else c.sdn
+        vec[sg] = (ed.slater_vector(Lt, states), ed.slater_vector(R, states))
+    L = np.outer(vec[1][0], vec[-1][0])
+    R = np.outer(vec[1][1], vec[-1][1])
+    want = c.s_afm(L, R, m.eps)
+    assert abs(got - want) < 1e-12
+    G = ch.G[1]
+    assert np.abs(G - G.T).max() > 1e-3                 # the asymmetric case
