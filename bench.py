@@ -268,7 +268,7 @@ def run_ours(a):
     ctx = pqmc.Context(specs, prec=PRECS[head], seed=2, n_stab=n_stab, chain_offset=rank * a.chains,
                        max_meas=a.steps + 1, stream=stream.cuda_stream)
     h2d = ctx.device_bytes()
-    rec = np.zeros((a.chains, 5))
+    rec = np.zeros((a.chains, pqmc.RECORD))
     d2h = 0
     for _ in range(a.steps):
         ctx.sweep(1, measure=True)

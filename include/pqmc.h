@@ -126,7 +126,11 @@ typedef struct {
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
  * consecutive sweeps (errors are NaN with fewer than two bins). E is the
- * energy per site of Eq. (2); docc the double occupancy per site. */
+ * energy per site of Eq. (2); docc the double occupancy per site; s_afm the
+ * AFM structure factor of the Fig. 2 comparison, taken as its z component
+ * (1/N^2) sum_ij eps_i eps_j <S^z_i S^z_j>, S^z_i = (n_i,up - n_i,dn)/2 and
+ * eps_i = +1 on sublattice A, -1 on B (the paper defers the definition to its
+ * supplement). */
 typedef struct {
     double E, E_err;
     double docc, docc_err;
@@ -134,6 +138,7 @@ typedef struct {
     double accept;          /* accepted / proposed flips */
     double max_dG;          /* max |G - G_fresh| over all stabilisations so far */
     long n_meas;            /* measurements used */
+    double s_afm, s_afm_err;
 } pqmc_obs;
 
 typedef struct pqmc_ctx pqmc_ctx;
@@ -167,14 +172,15 @@ pqmc_status pqmc_synchronize(pqmc_ctx* ctx);
  * meaningful when the chains share one spec). Synchronises first. */
 pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out);
 
-/* Raw per-sweep records of one chain: out[m*5 + {0..4}] = (sign of the weight
+/* Raw per-sweep records of one chain: out[m*6 + {0..5}] = (sign of the weight
  * from the stabilised stacks, E/site, docc/site, kinetic energy/site, running
- * product of sgn(R) over accepted flips) for m < *n; on entry *n is the
- * capacity in records, on return the number written. Synchronises first. */
+ * product of sgn(R) over accepted flips, S_AFM of this configuration) for
+ * m < *n; on entry *n is the capacity in records, on return the number
+ * written. Synchronises first. */
 pqmc_status pqmc_get_measurements(pqmc_ctx* ctx, int chain, double* out, long* n);
 
 /* Latest measurement record of every chain in one device-to-host copy:
- * out[c*5 + {0..4}] as in pqmc_get_measurements (n_chains x 5 doubles; NaN
+ * out[c*6 + {0..5}] as in pqmc_get_measurements (n_chains x 6 doubles; NaN
  * for a chain that has no record yet). Synchronises first. */
 pqmc_status pqmc_get_last_records(pqmc_ctx* ctx, double* out);
 

@@ -37,7 +37,7 @@ struct HostChain {
   pqmc_chain_spec spec;
   int N, ld, nup, ndn, nmax, Ltau, nb;
   size_t off_fields, off_G, off_Rst, off_Lst, off_Rlog, off_Llog, off_meas, off_dG,
-      off_acc, off_state, off_P, off_scratch, off_expKm, off_expKp, off_expKm64, off_K64;
+      off_acc, off_state, off_P, off_scratch, off_expKm, off_expKp, off_expKm64, off_K64, off_eps;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -213,6 +213,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
       take(Tm);
       take((size_t)h.N * h.N * 8);
       take((size_t)h.N * h.N * 8);
+      take((size_t)h.N * 8);
       model_off[key] = o1;
     }
     const ModelTables& mt = models[key];
@@ -232,6 +233,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     h.off_expKp = h.off_expKm + align_up((size_t)h.N * h.ld * ctx->tsize, 256);
     h.off_expKm64 = h.off_expKp + align_up((size_t)h.N * h.ld * ctx->tsize, 256);
     h.off_K64 = h.off_expKm64 + align_up((size_t)h.N * h.N * 8, 256);
+    h.off_eps = h.off_K64 + align_up((size_t)h.N * h.N * 8, 256);
     const size_t Gbytes = 2ull * h.N * h.ld * ctx->tsize;
     const size_t blk = (size_t)h.N * h.nmax * 8;
     h.off_fields = take((size_t)(h.Ltau + 2) * h.N);
@@ -280,6 +282,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
       }
       put<double>(A, h.off_expKm64, mt.expKm, h.N, h.N, h.N);
       put<double>(A, h.off_K64, mt.K, h.N, h.N, h.N);
+      memcpy(A.data() + h.off_eps, mt.eps.data(), (size_t)h.N * 8);
       written[key] = true;
     }
     // P_sigma column-major (ld N) in blocks of N x nmax
@@ -342,6 +345,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.expKp = b + h.off_expKp;
     d.expKm64 = reinterpret_cast<const double*>(b + h.off_expKm64);
     d.K64 = reinterpret_cast<const double*>(b + h.off_K64);
+    d.eps = reinterpret_cast<const double*>(b + h.off_eps);
     d.P = reinterpret_cast<const double*>(b + h.off_P);
     d.Rst = reinterpret_cast<double*>(b + h.off_Rst);
     d.Lst = reinterpret_cast<double*>(b + h.off_Lst);
@@ -481,7 +485,7 @@ pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
   long long prop = 0, acc = 0;
   double maxdG = 0;
   long nm = 0;
-  std::vector<std::vector<double>> per_s, per_E, per_D;
+  std::vector<std::vector<double>> per_s, per_E, per_D, per_S;
   for (int c = c0; c < c1; ++c) {
     std::vector<double> rec;
     int n = 0;
@@ -492,20 +496,22 @@ pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
     acc += st.n_acc;
     maxdG = std::max(maxdG, st.max_dG);
     nm += n;
-    std::vector<double> sv(n), Ev(n), Dv(n);
+    std::vector<double> sv(n), Ev(n), Dv(n), Sv(n);
     for (int m = 0; m < n; ++m) {
       sv[m] = rec[(size_t)m * kRecord + 0];
       Ev[m] = sv[m] * rec[(size_t)m * kRecord + 1];
       Dv[m] = sv[m] * rec[(size_t)m * kRecord + 2];
+      Sv[m] = sv[m] * rec[(size_t)m * kRecord + 5];
     }
     per_s.push_back(sv);
     per_E.push_back(Ev);
     per_D.push_back(Dv);
+    per_S.push_back(Sv);
   }
   // groups: chains when pooling several, else up to 20 bins of consecutive sweeps
-  std::vector<std::vector<double>> bs, bE, bD;
+  std::vector<std::vector<double>> bs, bE, bD, bS;
   if (per_s.size() >= 2) {
-    bs = per_s; bE = per_E; bD = per_D;
+    bs = per_s; bE = per_E; bD = per_D; bS = per_S;
   } else if (!per_s.empty()) {
     const int n = (int)per_s[0].size();
     const int nbins = std::max(1, std::min(n, 20));
@@ -514,6 +520,7 @@ pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
       bs.emplace_back(per_s[0].begin() + b * per, per_s[0].begin() + (b + 1) * per);
       bE.emplace_back(per_E[0].begin() + b * per, per_E[0].begin() + (b + 1) * per);
       bD.emplace_back(per_D[0].begin() + b * per, per_D[0].begin() + (b + 1) * per);
+      bS.emplace_back(per_S[0].begin() + b * per, per_S[0].begin() + (b + 1) * per);
     }
   }
   memset(out, 0, sizeof *out);
@@ -522,10 +529,12 @@ pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
   out->max_dG = maxdG;
   if (nm == 0 || bs.empty()) {
     out->E = out->E_err = out->docc = out->docc_err = out->sign = out->sign_err = NAN;
+    out->s_afm = out->s_afm_err = NAN;
     return PQMC_OK;
   }
   estimate(bE, bs, out->E, out->E_err);
   estimate(bD, bs, out->docc, out->docc_err);
+  estimate(bS, bs, out->s_afm, out->s_afm_err);
   // average sign: mean of s with the same grouping
   std::vector<std::vector<double>> ones;
   for (auto& g : bs) ones.emplace_back(g.size(), 1.0);

@@ -10,7 +10,7 @@ constexpr int kMaxN = 1024;       // sites per chain
 constexpr int kMaxSigma = 512;    // particles per spin
 constexpr int kQRParts = 8;       // row chunks of the column dots in the Householder QR
 constexpr int kThreads = 256;     // threads per chain CTA
-constexpr int kRecord = 5;        // doubles per measurement record
+constexpr int kRecord = 6;        // doubles per measurement record
 constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
 
 // phases timed with clock64() by thread 0 of each chain CTA
@@ -56,6 +56,7 @@ struct ChainDesc {
   const void* expKp;       // N x ld (T): e^{+dtau K}
   const double* expKm64;   // N x N FP64
   const double* K64;       // N x N FP64
+  const double* eps;       // N: staggered sublattice sign (+1 A, -1 B)
   const double* P;         // 2 x (N x nmax) FP64, column-major per spin (ld N)
   double* Rst;             // (nb+1) x 2 x (N x nmax) FP64
   double* Lst;             // (nb+1) x 2 x (N x nmax) FP64

@@ -1,1206 +1,9 @@
-// PQMC sweep kernels for GB300 (sm_103a).
-//
-// One CTA owns one Markov chain for the whole launch and runs complete
-// sweeps: Metropolis flips of the Ising fields with delayed (blocked)
-// updates, slice wrapping, QR stabilisation of the B_L / B_R stacks, and the
-// measurement at the middle slice.  Chains are independent, so a batch of
-// chains of uneven size is one launch with one CTA per chain.
-//
-// Paper: Method section (PQMC estimator, Eq. (1) HS of the Gutzwiller
-// factor) and honeycomb Hubbard section (Eq. (2), trial state of Eq. (3)).
-//
-// Conventions (shared with the header):
-//   slices tau = 0..Ltau+1; 0 and Ltau+1 carry the Gutzwiller fields;
-//   B_tau = e^{-dtau K} e^{V(s_tau)} (interaction), e^{V(s_tau)} (Gutzwiller);
-//   G(tau) = 1 - B_R(tau) (B_L(tau) B_R(tau))^{-1} B_L(tau),
-//   B_R(tau) = B_tau ... B_0 P,  B_L(tau) = P^T B_{Ltau+1} ... B_{tau+1}.
-//   A flip of s_{tau,i} is proposed on G(tau-1): R_sigma = 1 + Delta_sigma (1 - G_ii).
-//
-// Precision: T (double or float) is the path precision of G, the ratios,
-// the wrap, the delayed updates, the products that advance the stack blocks
-// and the assembly of G from them.  The Householder QR of the stack blocks,
-// the product Q_L^T Q_R, its inverse and the log-determinant / sign are FP64
-// in every path.
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include <cmath>
-#include <cstring>
-#include <mutex>
-#include <string>
-#include <type_traits>
-#include <vector>
-
-#include "../../include/pqmc.h"
-#include "chain.h"
-#include "model.h"
-#include "philox.cuh"
+// Host side of the sweep kernels: shared-memory budgets, the precision and
+// CTA-shape dispatch over the per-path translation units, the sweep-index
+// advance kernel, and the allocation-free single-chain initialisation.
+#include "sweep_kernels.cuh"
 
 namespace pqmc {
-
-
-// --------------------------------------------------------------------------
-// small CTA helpers
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Loop over a 2D index range with warps along rows and lanes along columns
-// (no runtime integer division in the element loops).
-#define PQMC_FOR_2D(i, i0, i1, j, j0, j1)                                          \
-  for (int i = (i0) + (int)(threadIdx.x >> 5); i < (i1); i += (int)(blockDim.x >> 5)) \
-    for (int j = (j0) + (int)(threadIdx.x & 31); j < (j1); j += 32)
-
-// Sum / max over the CTA; every thread gets the result.  red holds >= 32 doubles.
-__device__ double cta_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = lane < nw ? red[lane] : 0.0;
-  return warp_sum(t);
-}
-__device__ double cta_max(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_max(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = lane < nw ? red[lane] : 0.0;
-  return warp_max(t);
-}
-
-// --------------------------------------------------------------------------
-// CTA-wide register-tiled GEMM: C = A B, A(i,k) = A[i*sai + k*sak],
-// B(k,j) = B[k*sbk + j*sbj]; inputs are converted to the accumulation type T
-// on load; the epilogue receives (i, j, value).  Every thread owns 4x4
-// outputs.  When A is contiguous in i and B in j (sai = sbj = 1, strides and
-// pointers 16-byte aligned, same type as T) the operands are read with
-// 16-byte vector loads.
-
-struct EpiStore {
-  static constexpr bool kRow4 = true;   // supports 4 contiguous outputs of a row at once
-  template <typename T, typename TC> __device__ void operator()(TC* C, int sci, int scj, int i, int j, T v) const {
-    C[(long)i * sci + (long)j * scj] = (TC)v;
-  }
-  template <typename T> __device__ void row4(T* c, const T v[4]) const { c[0] = v[0]; c[1] = v[1]; c[2] = v[2]; c[3] = v[3]; }
-};
-struct EpiSub {
-  static constexpr bool kRow4 = true;
-  template <typename T, typename TC> __device__ void operator()(TC* C, int sci, int scj, int i, int j, T v) const {
-    C[(long)i * sci + (long)j * scj] -= (TC)v;
-  }
-  template <typename T> __device__ void row4(T* c, const T v[4]) const {
-    c[0] -= v[0]; c[1] -= v[1]; c[2] -= v[2]; c[3] -= v[3];
-  }
-};
-template <typename E, typename = void> struct HasRow4 { static constexpr bool value = false; };
-template <typename E> struct HasRow4<E, std::void_t<decltype(E::kRow4)>> { static constexpr bool value = E::kRow4; };
-
-template <typename T> struct Vec4;
-template <> struct Vec4<float> {
-  __device__ static void load(const float* p, float v[4]) {
-    const float4 x = *reinterpret_cast<const float4*>(p);
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-  }
-  static constexpr int kAlign = 4;
-};
-template <> struct Vec4<double> {
-  __device__ static void load(const double* p, double v[4]) {
-    const double2 x = *reinterpret_cast<const double2*>(p);
-    const double2 y = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-  }
-  static constexpr int kAlign = 2;
-};
-
-template <typename T>
-__device__ __forceinline__ bool vec_ok(const T* p, long stride) {
-  return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && (stride % Vec4<T>::kAlign == 0);
-}
-
-template <typename T, typename TA, typename TB, typename TC, typename Epi>
-__device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, const TB* B, int sbk, int sbj,
-                         TC* C, int sci, int scj, Epi epi) {
-  const int tm = (M + 3) >> 2, tn = (Nn + 3) >> 2;
-  bool vec = false, vec_row = false, st_row = false;
-  if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
-    vec = sai == 1 && sbj == 1 && vec_ok<T>((const T*)A, sak) && vec_ok<T>((const T*)B, sbk) &&
-          (M % 4 == 0) && (Nn % 4 == 0);
-    // A contiguous along k (row-major): 4 x 4 blocks of A per four k-steps
-    vec_row = !vec && sak == 1 && sbj == 1 && vec_ok<T>((const T*)A, sai) && vec_ok<T>((const T*)B, sbk) &&
-              (M % 4 == 0) && (Nn % 4 == 0) && (K % 4 == 0);
-  }
-  if constexpr (std::is_same<T, TC>::value && HasRow4<Epi>::value) {
-    st_row = scj == 1 && vec_ok<T>((const T*)C, sci) && (Nn % 4 == 0);
-  }
-  for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
-    const int i0 = (t / tn) << 2, j0 = (t % tn) << 2;
-    T acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
-    if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
-      if (vec) {
-        const T* pa = (const T*)A + i0;
-        const T* pb = (const T*)B + j0;
-#pragma unroll 4
-        for (int k = 0; k < K; ++k) {
-          T a[4], b[4];
-          Vec4<T>::load(pa + (long)k * sak, a);
-          Vec4<T>::load(pb + (long)k * sbk, b);
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
-        }
-      }
-    }
-    if constexpr (std::is_same<T, TA>::value && std::is_same<T, TB>::value) {
-      if (vec_row) {
-        const T* pa = (const T*)A + (long)i0 * sai;
-        const T* pb = (const T*)B + j0;
-        for (int k = 0; k < K; k += 4) {
-          T a[4][4], b[4][4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) Vec4<T>::load(pa + (long)r * sai + k, a[r]);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) Vec4<T>::load(pb + (long)(k + kk) * sbk, b[kk]);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r][kk], b[kk][q], acc[r][q]);
-        }
-      }
-    }
-    if (!vec && !vec_row) {
-      for (int k = 0; k < K; ++k) {
-        T a[4], b[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = (i0 + r < M) ? (T)A[(long)(i0 + r) * sai + (long)k * sak] : T(0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = (j0 + q < Nn) ? (T)B[(long)k * sbk + (long)(j0 + q) * sbj] : T(0);
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
-      }
-    }
-    if constexpr (std::is_same<T, TC>::value && HasRow4<Epi>::value) {
-      if (st_row) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (i0 + r < M) epi.row4((T*)C + (long)(i0 + r) * sci + j0, acc[r]);
-        continue;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (i0 + r < M && j0 + q < Nn) epi(C, sci, scj, i0 + r, j0 + q, acc[r][q]);
-  }
-}
-
-// --------------------------------------------------------------------------
-// Split-precision tensor-core GEMM (the BF16X3 path): C = A B for FP32 A, B
-// with every operand split as x = hi + lo, hi = bf16(x), lo = bf16(x - hi),
-// and C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 by
-// mma.sync.m16n8k16 (Henry, Tang & Heinecke 2019 use the same split).  Each
-// warp owns 16 x 8 output tiles; operands are read with arbitrary strides
-// (zero outside the matrix) and split on the fly.
-
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
-  h = __float2bfloat16_rn(v);
-  l = __float2bfloat16_rn(v - __bfloat162float(h));
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 first, __nv_bfloat16 second) {
-  return (uint32_t)__bfloat16_as_ushort(first) | ((uint32_t)__bfloat16_as_ushort(second) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <typename Epi>
-__device__ void cta_gemm_bf16x3(int M, int Nn, int K, const float* A, int sai, int sak, const float* B, int sbk,
-                                int sbj, float* C, int sci, int scj, Epi epi) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int g = lane >> 2, tg = lane & 3;
-  const int tm = (M + 15) >> 4, tn = (Nn + 7) >> 3;
-  auto a_at = [&](int r, int k) -> float { return (r < M && k < K) ? A[(long)r * sai + (long)k * sak] : 0.0f; };
-  auto b_at = [&](int k, int n) -> float { return (k < K && n < Nn) ? B[(long)k * sbk + (long)n * sbj] : 0.0f; };
-  for (int t = warp; t < tm * tn; t += nw) {
-    const int m0 = (t / tn) << 4, n0 = (t % tn) << 3;
-    const int r0 = m0 + g, r1 = m0 + g + 8, nn = n0 + g;
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 0; k0 < K; k0 += 16) {
-      const int k = k0 + 2 * tg;
-      const float av[8] = {a_at(r0, k), a_at(r0, k + 1), a_at(r1, k), a_at(r1, k + 1),
-                           a_at(r0, k + 8), a_at(r0, k + 9), a_at(r1, k + 8), a_at(r1, k + 9)};
-      const float bv[4] = {b_at(k, nn), b_at(k + 1, nn), b_at(k + 8, nn), b_at(k + 9, nn)};
-      __nv_bfloat16 ah[8], al[8], bh[4], bl[4];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) split_bf16(av[q], ah[q], al[q]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) split_bf16(bv[q], bh[q], bl[q]);
-      const uint32_t AH[4] = {pack2(ah[0], ah[1]), pack2(ah[2], ah[3]), pack2(ah[4], ah[5]), pack2(ah[6], ah[7])};
-      const uint32_t AL[4] = {pack2(al[0], al[1]), pack2(al[2], al[3]), pack2(al[4], al[5]), pack2(al[6], al[7])};
-      const uint32_t BH[2] = {pack2(bh[0], bh[1]), pack2(bh[2], bh[3])};
-      const uint32_t BL[2] = {pack2(bl[0], bl[1]), pack2(bl[2], bl[3])};
-      mma_bf16(c, AH, BL);
-      mma_bf16(c, AL, BH);
-      mma_bf16(c, AH, BH);
-    }
-    const int cc = n0 + 2 * tg;
-    if (r0 < M) {
-      if (cc < Nn) epi(C, sci, scj, r0, cc, c[0]);
-      if (cc + 1 < Nn) epi(C, sci, scj, r0, cc + 1, c[1]);
-    }
-    if (r1 < M) {
-      if (cc < Nn) epi(C, sci, scj, r1, cc, c[2]);
-      if (cc + 1 < Nn) epi(C, sci, scj, r1, cc + 1, c[3]);
-    }
-  }
-}
-
-// Path GEMM of the wrap and of the delayed update: split-precision tensor
-// cores when the chain runs the BF16X3 path, CUDA-core FMA otherwise.
-template <typename T, typename Epi>
-__device__ void path_gemm(const ChainDesc& c, int M, int Nn, int K, const T* A, int sai, int sak, const T* B, int sbk,
-                          int sbj, T* C, int sci, int scj, Epi epi) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (c.tc) {
-      cta_gemm_bf16x3(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
-      return;
-    }
-  }
-  cta_gemm<T>(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
-}
-
-// --------------------------------------------------------------------------
-// shared memory of one chain CTA
-
-// Buffers of one flip block (lives in shared memory, see make_cta).
-template <typename T>
-struct FlipBuf {
-  T Gb[2][kBlock][kBlock + 1];      // diagonal block of current G, both spins
-  T Tu[2][kBlock][kBlock + 1];      // 1 + (1 - G_SS) Gamma, inverted in place, then M
-  T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
-  double u[kBlock];                 // Metropolis uniforms of the block
-  float uf[kBlock];                 // the same rounded down to 24 bits (FP32 decisions)
-  int sites[kBlock];                // block index of each accepted flip
-  int fl[kBlock];                   // fields of the block
-};
-
-template <typename T>
-struct Smem {
-  ChainDesc desc;                   // this chain's descriptor, copied in at launch
-  double red[32];                   // reduction scratch
-  double vtab[2][2][2];             // e^{sigma kappa s}: [Gutzwiller?][spin][s = -1?]
-  T vt[2][2][2];                    // the same in the path precision
-  T vti[2][2][2];                   // and its inverse
-  long long cyc[kPhases];           // per-phase clock cycles (thread 0)
-  long long t_mark;
-  signed char fr[kMaxN];            // fields of the staged slice
-  int na;                           // accepted flips in the block
-  int piv;
-  int nswap[2];
-  int staged;                       // slice held in fr, or -1
-  double sign_running;
-  double sign_spin[2];
-  double logw_spin[2];
-  double dGmax;
-  long long n_prop, n_acc, acc_pos;
-  int err;
-};
-
-// One chain CTA: its descriptor, shared memory, and where G and the phase
-// scratch live (shared memory when they fit, else the chain's global buffers).
-template <typename T>
-struct Cta {
-  const ChainDesc& c;
-  Smem<T>& sh;
-  uint64_t seed;
-  T* Gp;
-  unsigned char* scr;
-  ScratchLayout L;
-  bool resident;
-  FlipBuf<T>* fb;
-  __device__ T* G(int s) const { return Gp + (long)s * c.N * c.ld; }
-  __device__ T* Gt() const { return reinterpret_cast<T*>(scr + L.gt); }
-  __device__ T* Ub() const { return reinterpret_cast<T*>(scr + L.u); }
-  __device__ T* Wb() const { return reinterpret_cast<T*>(scr + L.w); }
-  __device__ double* M64() const { return reinterpret_cast<double*>(scr + L.m64); }
-  __device__ double* Q64() const { return reinterpret_cast<double*>(scr + L.mtq); }
-  __device__ T* Mt() const { return reinterpret_cast<T*>(scr + L.mtq); }
-  __device__ T* Mt2() const { return reinterpret_cast<T*>(scr + L.mt2); }
-  __device__ double* qbeta() const { return reinterpret_cast<double*>(scr + L.qaux); }
-  __device__ double* qalpha() const { return qbeta() + c.nmax; }
-  __device__ double* qw() const { return qbeta() + 2 * c.nmax; }
-  __device__ double* qpart() const { return qbeta() + 3 * c.nmax; }
-  __device__ double* Ob(int s) const {
-    return reinterpret_cast<double*>(scr + L.o + s * al16((size_t)c.nmax * c.nmax * 8));
-  }
-  __device__ T* Yb() const { return reinterpret_cast<T*>(scr + L.y); }
-  __device__ T* QRt() const { return reinterpret_cast<T*>(scr + L.qrt); }
-  __device__ T* QLt() const { return reinterpret_cast<T*>(scr + L.qlt); }
-  __device__ double* pval(int s) const { return reinterpret_cast<double*>(scr + L.laux) + s * 3 * c.nmax; }
-  __device__ double* pinv(int s) const { return pval(s) + c.nmax; }
-  __device__ double* lmul(int s) const { return pval(s) + 2 * c.nmax; }
-  __device__ const T* Em() const { return reinterpret_cast<const T*>(c.expKm); }
-  __device__ const T* Ep() const { return reinterpret_cast<const T*>(c.expKp); }
-  __device__ int nsig(int s) const { return s == 0 ? c.nup : c.ndn; }
-  __device__ bool gutz(int tau) const { return tau == 0 || tau == c.Ltau + 1; }
-  // stage the fields of slice tau into shared memory (collective)
-  __device__ void stage(int tau) {
-    __syncthreads();
-    const int8_t* f = c.fields + (long)tau * c.N;
-    for (int i = threadIdx.x; i < c.N; i += blockDim.x) sh.fr[i] = f[i];
-    if (threadIdx.x == 0) sh.staged = tau;
-    __syncthreads();
-  }
-  // diagonal of e^{V_sigma(s_tau)} at site i for the staged slice tau
-  __device__ double vexp(int tau, int s, int i) const {
-    return sh.vtab[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
-  }
-  __device__ T vexpT(int tau, int s, int i) const { return sh.vt[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1]; }
-  __device__ T vinvT(int tau, int s, int i) const { return sh.vti[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1]; }
-  // charge the cycles since the last mark to phase ph (thread 0 only)
-  __device__ void mark(int ph) {
-    if (threadIdx.x == 0) {
-      const long long t = clock64();
-      sh.cyc[ph] += t - sh.t_mark;
-      sh.t_mark = t;
-    }
-  }
-};
-
-// --------------------------------------------------------------------------
-// Metropolis updates of one slice with delayed updates in blocks of kBlock
-// sites.  Inside a block one warp (lane = column of the block) proposes the
-// flips in order on the kBlock x kBlock diagonal block of G.  Later proposals
-// read only rows and columns of later sites, so an accepted flip at j updates
-// just that future part: G_rq += c G_rj G_jq (r, q > j), c = Delta/R_sigma.
-// After the block the whole CTA applies the accepted set S at once:
-//     G <- G - (E_S - G_{:,S}) M G_{S,:},  M = Gamma (1 + (1 - G_SS) Gamma)^{-1},
-// G the G of the block start, Gamma = diag(Delta) of the accepted flips.  This
-// equals the sequence of Sherman-Morrison updates because the new G depends
-// only on the new fields; the pivots of the a x a inverse are the accepted
-// ratios, so Gauss-Jordan without pivoting follows the sequential process.
-
-template <typename T>
-__device__ __forceinline__ bool metropolis_accept(double u, float uf, T R) {
-  if constexpr (std::is_same<T, double>::value) return u < fabs(R);
-  else return uf < fabsf(R);
-}
-
-template <typename T>
-__device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
-  const ChainDesc& c = x.c;
-  Smem<T>& sh = x.sh;
-  FlipBuf<T>& fb = *x.fb;
-  const int N = c.N, ld = c.ld;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int kap = x.gutz(tau) ? 1 : 0;
-  int8_t* f = c.fields + (long)tau * N;
-  T* Ubuf = x.Ub();                                    // kBlock x N  (U column-major, ld N)
-  T* Wbuf = x.Wb();                                    // kBlock x ld (rows G_{S,:})
-  const T dl[2][2] = {{(T)c.delta[kap][0][0], (T)c.delta[kap][0][1]}, {(T)c.delta[kap][1][0], (T)c.delta[kap][1][1]}};
-
-  for (int i0 = 0; i0 < N; i0 += kBlock) {
-    const int nbk = min(kBlock, N - i0);
-    for (int e = threadIdx.x; e < 2 * kBlock * kBlock; e += blockDim.x) {
-      const int s = e / (kBlock * kBlock), r = (e / kBlock) % kBlock, q = e % kBlock;
-      fb.Gb[s][r][q] = (r < nbk && q < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + q] : T(0);
-    }
-    if (threadIdx.x < kBlock) {
-      const int j = threadIdx.x;
-      if (j < nbk) {
-        const U4 w = philox4x32_10((uint32_t)(i0 + j), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
-                                   (uint32_t)(x.seed >> 32));
-        const uint64_t m53 = ((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11);
-        fb.u[j] = (double)m53 * 0x1.0p-53;
-        fb.uf[j] = (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;   // the same uniform rounded down to 24 bits
-      } else {
-        fb.u[j] = 2.0;
-        fb.uf[j] = 2.0f;
-      }
-      fb.fl[j] = j < nbk ? (int)f[i0 + j] : 1;
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-      int a = 0;
-      for (int j = 0; j < nbk; ++j) {
-        const int si = fb.fl[j] > 0 ? 0 : 1;
-        const T d0 = dl[0][si], d1 = dl[1][si];
-        const T r0 = T(1) + d0 * (T(1) - fb.Gb[0][j][j]);
-        const T r1 = T(1) + d1 * (T(1) - fb.Gb[1][j][j]);
-        const T R = r0 * r1;
-        const bool acc = metropolis_accept<T>(fb.u[j], fb.uf[j], R);
-        if (lane == 0) {
-          if (!isfinite(R)) sh.err |= kErrNaN;
-          if (sh.acc_pos < c.acc_cap) c.acc_log[sh.acc_pos] = acc ? 1 : 0;
-          sh.acc_pos++;
-          sh.n_prop++;
-        }
-        if (!acc) continue;
-        const T c0 = d0 / r0, c1 = d1 / r1;
-        if (lane > j && lane < nbk) {
-          const T y0 = c0 * fb.Gb[0][j][lane], y1 = c1 * fb.Gb[1][j][lane];
-#pragma unroll 4
-          for (int r = j + 1; r < nbk; ++r) {
-            fb.Gb[0][r][lane] = fma(fb.Gb[0][r][j], y0, fb.Gb[0][r][lane]);
-            fb.Gb[1][r][lane] = fma(fb.Gb[1][r][j], y1, fb.Gb[1][r][lane]);
-          }
-        }
-        if (lane == 0) {
-          fb.sites[a] = j;
-          fb.cl[0][a] = d0;
-          fb.cl[1][a] = d1;
-          fb.fl[j] = -fb.fl[j];
-          f[i0 + j] = (int8_t)fb.fl[j];
-          sh.sign_running *= (R < T(0)) ? -1.0 : 1.0;
-          sh.n_acc++;
-        }
-        ++a;
-        __syncwarp();
-      }
-      if (lane == 0) sh.na = a;
-    }
-    __syncthreads();
-    x.mark(kPhFlip);
-    const int a = sh.na;
-    if (a == 0) continue;
-
-    // X = 1 + (1 - G_SS) Gamma (block-start G), inverted in place by one warp
-    // per spin; then M = Gamma X^{-1} (stored in Tu)
-    PQMC_FOR_2D(sl, 0, 2 * a, m, 0, a) {
-      const int s = sl >= a ? 1 : 0, l = sl - s * a;
-      const T g = x.G(s)[(long)(i0 + fb.sites[l]) * ld + i0 + fb.sites[m]];
-      fb.Tu[s][l][m] = ((l == m) ? T(1) : T(0)) + ((l == m ? T(1) : T(0)) - g) * fb.cl[s][m];
-    }
-    __syncthreads();
-    if (warp < 2) {
-      const int s = warp;
-      T (*X)[kBlock + 1] = fb.Tu[s];
-      for (int p = 0; p < a; ++p) {
-        const T ip = T(1) / X[p][p];
-        const T xpl = lane < a ? X[p][lane] : T(0);
-        if (lane < a && lane != p)
-          for (int r = 0; r < a; ++r)
-            if (r != p) X[r][lane] = fma(-X[r][p] * ip, xpl, X[r][lane]);
-        __syncwarp();
-        if (lane < a) {
-          if (lane != p) X[p][lane] = xpl * ip;
-          X[lane][p] = lane == p ? ip : -X[lane][p] * ip;
-        }
-        __syncwarp();
-      }
-      for (int l = 0; l < a; ++l)
-        if (lane < a) X[l][lane] *= fb.cl[s][l];
-    }
-    __syncthreads();
-    // per spin: A_S = E_S - G_{:,S} (N x a, column-major) and W = G_{S,:}
-    // (a x N) gathered before G changes, then MW = M W and G -= A_S MW
-    T* MW = reinterpret_cast<T*>(x.scr + x.L.mw);
-    for (int s = 0; s < 2; ++s) {
-      T* Gs = x.G(s);
-      PQMC_FOR_2D(m, 0, a, i, 0, N) {
-        const int col = i0 + fb.sites[m];
-        Ubuf[(long)m * N + i] = (i == col ? T(1) : T(0)) - Gs[(long)i * ld + col];
-      }
-      PQMC_FOR_2D(l, 0, a, q, 0, N) Wbuf[(long)l * ld + q] = Gs[(long)(i0 + fb.sites[l]) * ld + q];
-      __syncthreads();
-      cta_gemm<T>(a, N, a, &fb.Tu[s][0][0], kBlock + 1, 1, Wbuf, ld, 1, MW, ld, 1, EpiStore());
-      __syncthreads();
-      path_gemm<T>(c, N, N, a, Ubuf, 1, N, MW, ld, 1, Gs, ld, 1, EpiSub());
-      __syncthreads();
-    }
-    x.mark(kPhFlush);
-  }
-}
-
-// --------------------------------------------------------------------------
-// Slice wrapping.  dir = +1: G(tau) = B_tau G(tau-1) B_tau^{-1};
-// dir = -1: G(tau-1) = B_tau^{-1} G(tau) B_tau.
-
-template <typename T>
-__device__ void wrap(Cta<T>& x, int tau, int dir) {
-  const ChainDesc& c = x.c;
-  const int N = c.N, ld = c.ld;
-  const bool gz = x.gutz(tau);
-  T* Gt = x.Gt();
-  x.stage(tau);
-  if (dir > 0) {
-    for (int s = 0; s < 2; ++s) {
-      T* Gs = x.G(s);
-      PQMC_FOR_2D(i, 0, N, j, 0, N) Gs[(long)i * ld + j] *= x.vexpT(tau, s, i) * x.vinvT(tau, s, j);
-    }
-    __syncthreads();
-    if (gz) return;
-    // Gt = e^{-dtau K} G, G = Gt e^{+dtau K}
-    for (int s = 0; s < 2; ++s) {
-      path_gemm<T>(c, N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
-      __syncthreads();
-      path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
-      __syncthreads();
-    }
-  } else {
-    if (!gz) {
-      for (int s = 0; s < 2; ++s) {
-        path_gemm<T>(c, N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
-        __syncthreads();
-        path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
-        __syncthreads();
-      }
-    }
-    for (int s = 0; s < 2; ++s) {
-      T* Gs = x.G(s);
-      PQMC_FOR_2D(i, 0, N, j, 0, N) Gs[(long)i * ld + j] *= x.vexpT(tau, s, j) * x.vinvT(tau, s, i);
-    }
-    __syncthreads();
-  }
-}
-
-// --------------------------------------------------------------------------
-// FP64 stabilisation.
-
-// log|prod_j d_j| and sign(prod_j d_j) of n values in shared memory, summed by
-// warp 0 and broadcast through shared memory (collective).
-template <typename T>
-__device__ void log_det_of(Cta<T>& x, const double* d, int n, int extra_sign_flips, double& logabs, double& sgn) {
-  Smem<T>& sh = x.sh;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (warp == 0) {
-    double la = 0.0;
-    int neg = 0;
-    for (int j = lane; j < n; j += 32) {
-      la += log(fabs(d[j]));
-      neg += d[j] < 0 ? 1 : 0;
-    }
-    la = warp_sum(la);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) neg += __shfl_xor_sync(0xffffffffu, neg, o);
-    if (lane == 0) {
-      sh.red[0] = la;
-      sh.red[1] = ((neg + extra_sign_flips) & 1) ? -1.0 : 1.0;
-    }
-  }
-  __syncthreads();
-  logabs = sh.red[0];
-  sgn = sh.red[1];
-  __syncthreads();
-}
-
-// Householder QR of the column-major N x n matrix M (ld N).  The explicit
-// orthonormal factor goes to Q (column-major, ld N); log|det R| and sign(det R)
-// are returned to every thread.  Each reflector is applied to all trailing
-// columns in three CTA-wide phases (partial column dots over row chunks, one
-// thread per column adds the chunks, a parallel rank-1 update), so no FP64
-// work sits in warp-shuffle reductions.
-template <typename T>
-__device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta, double* A, int c0, int c1, int j) {
-  double* part = x.qpart();
-  double* w = x.qw();
-  if (c1 <= c0) return;
-  // thread (col, p): rows j + p, j + p + kQRParts, ...
-  {
-    const int p = threadIdx.x & (kQRParts - 1);
-    for (int col = c0 + (int)(threadIdx.x / kQRParts); col < c1; col += (int)(blockDim.x / kQRParts)) {
-      const double* a = A + (long)col * N;
-      double d0 = 0.0, d1 = 0.0;
-      int i = j + p;
-      for (; i + kQRParts < N; i += 2 * kQRParts) {
-        d0 = fma(v[i], a[i], d0);
-        d1 = fma(v[i + kQRParts], a[i + kQRParts], d1);
-      }
-      if (i < N) d0 = fma(v[i], a[i], d0);
-      part[p * x.c.nmax + col] = d0 + d1;
-    }
-  }
-  __syncthreads();
-  for (int col = c0 + threadIdx.x; col < c1; col += blockDim.x) {
-    const int nm = x.c.nmax;
-    double q[kQRParts];
-#pragma unroll
-    for (int p = 0; p < kQRParts; ++p) q[p] = part[p * nm + col];
-#pragma unroll
-    for (int h = kQRParts / 2; h > 0; h >>= 1)
-#pragma unroll
-      for (int p = 0; p < h; ++p) q[p] += q[p + h];
-    w[col] = q[0] * beta;
-  }
-  __syncthreads();
-  {
-    const int rows = N - j, total = rows * (c1 - c0);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      const int cl = e / rows, i = j + (e - cl * rows), col = c0 + cl;
-      A[(long)col * N + i] = fma(-v[i], w[col], A[(long)col * N + i]);
-    }
-  }
-  __syncthreads();
-}
-
-// reflector of column j (warp 0): v = x - alpha e_j stored over the column
-template <typename T>
-__device__ void householder_reflector(Cta<T>& x, int N, double* M, int j) {
-  const int lane = threadIdx.x & 31;
-  if ((threadIdx.x >> 5) == 0) {
-    double* v = M + (long)j * N;
-    double s = 0.0;
-    for (int i = j + lane; i < N; i += 32) s = fma(v[i], v[i], s);
-    s = warp_sum(s);
-    if (lane == 0) {
-      const double x0 = v[j];
-      const double a = x0 > 0 ? -sqrt(s) : sqrt(s);
-      const double v0 = x0 - a;
-      const double vv = s - x0 * x0 + v0 * v0;
-      v[j] = v0;
-      x.qbeta()[j] = vv > 0 ? 2.0 / vv : 0.0;
-      x.qalpha()[j] = a;
-      if (a == 0.0) x.sh.err |= kErrStab;
-    }
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs, double& sgn) {
-  for (int j = 0; j < n; ++j) {
-    householder_reflector(x, N, M, j);
-    householder_apply(x, N, M + (long)j * N, x.qbeta()[j], M, j + 1, n, j);
-  }
-  x.mark(kPhQR);
-  PQMC_FOR_2D(col, 0, n, i, 0, N) Q[(long)col * N + i] = (i == col) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int j = n - 1; j >= 0; --j) householder_apply(x, N, M + (long)j * N, x.qbeta()[j], Q, j, n, j);
-  log_det_of(x, x.qalpha(), n, 0, logabs, sgn);
-  x.mark(kPhQRForm);
-}
-
-// Invert O_s (n_s x n_s, row-major) in place for both spins at once by
-// Gauss-Jordan elimination with partial pivoting (Golub & Van Loan, section
-// 3.2): warp s finds the pivot of spin s, swaps the rows, scales the pivot row
-// and saves the pivot column; the CTA then eliminates that column from every
-// other row; the row interchanges are undone on the columns at the end.
-// Returns log|det O_s| and sign(det O_s) to every thread.
-template <typename T>
-__device__ void gj_invert2(Cta<T>& x, const int n[2], double* O[2], double logabs[2], double sgn[2]) {
-  Smem<T>& sh = x.sh;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nmax = n[0] > n[1] ? n[0] : n[1];
-  if (threadIdx.x < 2) sh.nswap[threadIdx.x] = 0;
-  __syncthreads();
-  for (int j = 0; j < nmax; ++j) {
-    if (warp < 2 && j < n[warp]) {
-      const int s = warp, ns = n[s];
-      double* A = O[s];
-      double* f = x.lmul(s);
-      // pivot: largest |A_ij|, i >= j, ties to the lower row; |x| is compared
-      // through the bit pattern with the sign cleared, which orders
-      // non-negative doubles like their values
-      unsigned long long best = 0;
-      int bi = j;
-      for (int i = j + lane; i < ns; i += 32) {
-        const unsigned long long v = (unsigned long long)__double_as_longlong(A[(long)i * ns + j]) & 0x7fffffffffffffffull;
-        if (v > best || bi == j && i == j) { best = v; bi = i; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (bi != j) {
-        for (int col = lane; col < ns; col += 32) {
-          const double t = A[(long)j * ns + col];
-          A[(long)j * ns + col] = A[(long)bi * ns + col];
-          A[(long)bi * ns + col] = t;
-        }
-        if (lane == 0) sh.nswap[s]++;
-      }
-      if (lane == 0) x.pinv(s)[j] = (double)bi;         // row interchange of step j
-      __syncwarp();
-      const double pv = A[(long)j * ns + j];
-      const double ip = pv != 0.0 ? 1.0 / pv : 0.0;
-      if (lane == 0) {
-        x.pval(s)[j] = pv;
-        if (pv == 0.0) sh.err |= kErrStab;
-      }
-      for (int i = lane; i < ns; i += 32) f[i] = A[(long)i * ns + j];
-      __syncwarp();
-      for (int col = lane; col < ns; col += 32) A[(long)j * ns + col] = (col == j) ? ip : A[(long)j * ns + col] * ip;
-    }
-    __syncthreads();
-    x.mark(kPhGJPivot);
-    // eliminate column j from every other row of both spins: one FMA per
-    // element over a flat index (full warps on the FP64 pipe); the pivot
-    // column takes -f_i / pivot through the same FMA with a zero addend
-    {
-      const int e0 = j < n[0] ? n[0] * n[0] : 0;
-      const int e1 = j < n[1] ? n[1] * n[1] : 0;
-      for (int e = threadIdx.x; e < e0 + e1; e += blockDim.x) {
-        const int s = e < e0 ? 0 : 1;
-        const int ns = n[s], loc = e - (s ? e0 : 0);
-        const int i = loc / ns, col = loc - i * ns;
-        double* A = O[s];
-        const double fi = x.lmul(s)[i];
-        const double add = col == j ? 0.0 : A[(long)i * ns + col];
-        const double r = fma(-fi, A[(long)j * ns + col], add);
-        if (i != j) A[(long)i * ns + col] = r;
-      }
-    }
-    __syncthreads();
-    x.mark(kPhGJElim);
-  }
-  // undo the row interchanges on the columns, last step first
-  if (warp < 2) {
-    const int s = warp, ns = n[s];
-    double* A = O[s];
-    for (int j = ns - 1; j >= 0; --j) {
-      const int p = (int)x.pinv(s)[j];
-      if (p != j)
-        for (int i = lane; i < ns; i += 32) {
-          const double t = A[(long)i * ns + j];
-          A[(long)i * ns + j] = A[(long)i * ns + p];
-          A[(long)i * ns + p] = t;
-        }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  for (int s = 0; s < 2; ++s) log_det_of(x, x.pval(s), n[s], sh.nswap[s], logabs[s], sgn[s]);
-  x.mark(kPhGJTail);
-}
-
-// C = A^T B for column-major A, B (K x m and K x m', ld K): FP64, 2 x 2
-// outputs per thread, so that small products still occupy every warp.
-__device__ void gemm_tn_f64(int m, int mp, int K, const double* A, const double* B, double* C, int ldc) {
-  const int tm = (m + 1) >> 1, tn = (mp + 1) >> 1;
-  for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
-    const int i0 = (t / tn) << 1, j0 = (t % tn) << 1;
-    const double* a0 = A + (long)i0 * K;
-    const double* a1 = A + (long)min(i0 + 1, m - 1) * K;
-    const double* b0 = B + (long)j0 * K;
-    const double* b1 = B + (long)min(j0 + 1, mp - 1) * K;
-    double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      const double x0 = a0[k], x1 = a1[k], y0 = b0[k], y1 = b1[k];
-      c00 = fma(x0, y0, c00);
-      c01 = fma(x0, y1, c01);
-      c10 = fma(x1, y0, c10);
-      c11 = fma(x1, y1, c11);
-    }
-    C[(long)i0 * ldc + j0] = c00;
-    if (j0 + 1 < mp) C[(long)i0 * ldc + j0 + 1] = c01;
-    if (i0 + 1 < m) {
-      C[(long)(i0 + 1) * ldc + j0] = c10;
-      if (j0 + 1 < mp) C[(long)(i0 + 1) * ldc + j0 + 1] = c11;
-    }
-  }
-}
-
-__device__ void copy_block(const double* src, double* dst, int n) {
-  __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
-  __syncthreads();
-}
-
-template <typename T>
-__device__ double* stack_block(const Cta<T>& x, double* base, int b, int s) {
-  return base + ((long)b * 2 + s) * x.c.N * x.c.nmax;
-}
-
-// Right stack block b: QR of B_{b n} ... B_{(b-1)n+1} Q_R[b-1] (b >= 1) or of B_0 P (b = 0).
-// The slice products run in the path precision on a row-major copy.
-template <typename T>
-__device__ void push_R(Cta<T>& x, int b) {
-  const ChainDesc& c = x.c;
-  const int N = c.N, n_stab = c.n_stab;
-  double* M = x.M64();
-  for (int s = 0; s < 2; ++s) {
-    const int n = x.nsig(s);
-    const double* P = c.P + (long)s * N * c.nmax;
-    T* Mt = x.Mt();
-    T* Mt2 = x.Mt2();
-    double prev_l = 0.0, prev_s = 1.0;
-    if (b == 0) {
-      x.stage(0);
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = x.vexp(0, s, i) * P[(long)k * N + i];
-      __syncthreads();
-    } else {
-      const double* prev = stack_block(x, c.Rst, b - 1, s);
-      PQMC_FOR_2D(k, 0, n, i, 0, N) Mt[(long)i * n + k] = (T)prev[(long)k * N + i];
-      prev_l = c.Rlog[((b - 1) * 2 + s) * 2 + 0];
-      prev_s = c.Rlog[((b - 1) * 2 + s) * 2 + 1];
-      for (int tau = (b - 1) * n_stab + 1; tau <= b * n_stab; ++tau) {
-        x.stage(tau);
-        PQMC_FOR_2D(i, 0, N, k, 0, n) Mt[(long)i * n + k] *= x.vexpT(tau, s, i);
-        __syncthreads();
-        cta_gemm<T>(N, n, N, x.Em(), 1, c.ld, Mt, n, 1, Mt2, n, 1, EpiStore());
-        __syncthreads();
-        T* t = Mt; Mt = Mt2; Mt2 = t;
-      }
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
-      __syncthreads();
-    }
-    double la, sg;
-    x.mark(kPhStack);
-    qr_householder(x, N, n, M, x.Q64(), la, sg);
-    copy_block(x.Q64(), stack_block(x, c.Rst, b, s), N * n);
-    x.mark(kPhQR);
-    if (threadIdx.x == 0) {
-      c.Rlog[(b * 2 + s) * 2 + 0] = prev_l + la;
-      c.Rlog[(b * 2 + s) * 2 + 1] = prev_s * sg;
-    }
-    __syncthreads();
-  }
-}
-
-// Left stack block b holds (B_L(b n))^T = Q T^T: QR of
-// B_{bn+1}^T ... B_{(b+1)n}^T Q_L[b+1] (b < nb) or of e^{V(s_{Ltau+1})} P (b = nb).
-template <typename T>
-__device__ void push_L(Cta<T>& x, int b) {
-  const ChainDesc& c = x.c;
-  const int N = c.N, n_stab = c.n_stab;
-  double* M = x.M64();
-  for (int s = 0; s < 2; ++s) {
-    const int n = x.nsig(s);
-    const double* P = c.P + (long)s * N * c.nmax;
-    T* Mt = x.Mt();
-    T* Mt2 = x.Mt2();
-    double prev_l = 0.0, prev_s = 1.0;
-    if (b == c.nb) {
-      x.stage(c.Ltau + 1);
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = x.vexp(c.Ltau + 1, s, i) * P[(long)k * N + i];
-      __syncthreads();
-    } else {
-      const double* prev = stack_block(x, c.Lst, b + 1, s);
-      PQMC_FOR_2D(k, 0, n, i, 0, N) Mt[(long)i * n + k] = (T)prev[(long)k * N + i];
-      prev_l = c.Llog[((b + 1) * 2 + s) * 2 + 0];
-      prev_s = c.Llog[((b + 1) * 2 + s) * 2 + 1];
-      __syncthreads();
-      for (int tau = (b + 1) * n_stab; tau > b * n_stab; --tau) {
-        cta_gemm<T>(N, n, N, x.Em(), 1, c.ld, Mt, n, 1, Mt2, n, 1, EpiStore());
-        x.stage(tau);
-        PQMC_FOR_2D(i, 0, N, k, 0, n) Mt[(long)i * n + k] = x.vexpT(tau, s, i) * Mt2[(long)i * n + k];
-        __syncthreads();
-      }
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
-      __syncthreads();
-    }
-    double la, sg;
-    x.mark(kPhStack);
-    qr_householder(x, N, n, M, x.Q64(), la, sg);
-    copy_block(x.Q64(), stack_block(x, c.Lst, b, s), N * n);
-    x.mark(kPhQR);
-    if (threadIdx.x == 0) {
-      c.Llog[(b * 2 + s) * 2 + 0] = prev_l + la;
-      c.Llog[(b * 2 + s) * 2 + 1] = prev_s * sg;
-    }
-    __syncthreads();
-  }
-}
-
-// Fused epilogue of the G assembly: g = delta_ij - v, compare with the
-// propagated G, overwrite it.
-template <typename T>
-struct EpiFresh {
-  T* G;
-  int ld;
-  T* dmax;
-  template <typename A, typename TC> __device__ void operator()(TC*, int, int, int i, int j, A v) const {
-    const T g = (i == j ? T(1) : T(0)) - (T)v;
-    T& ref = G[(long)i * ld + j];
-    const T d = fabs(ref - g);
-    *dmax = d > *dmax ? d : *dmax;
-    ref = g;
-  }
-};
-
-// G <- 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T at stabilisation point b; records
-// max |G - G_fresh| when record != 0, and the weight's log|det| and sign.
-template <typename T>
-__device__ void refresh(Cta<T>& x, int b, bool record) {
-  const ChainDesc& c = x.c;
-  Smem<T>& sh = x.sh;
-  const int N = c.N, ld = c.ld;
-  T* Y = x.Yb();
-  T dmax = T(0);
-  double sign_total = 1.0;
-  int n[2] = {x.nsig(0), x.nsig(1)};
-  double* O[2] = {x.Ob(0), x.Ob(1)};
-  const double* QR[2] = {stack_block(x, c.Rst, b, 0), stack_block(x, c.Rst, b, 1)};
-  const double* QL[2] = {stack_block(x, c.Lst, b, 0), stack_block(x, c.Lst, b, 1)};
-  // O_s = Q_L^T Q_R and its inverse in FP64, both spins together
-  for (int s = 0; s < 2; ++s) gemm_tn_f64(n[s], n[s], N, QL[s], QR[s], O[s], n[s]);
-  __syncthreads();
-  x.mark(kPhOverlap);
-  double la[2], sg[2];
-  gj_invert2(x, n, O, la, sg);
-  x.mark(kPhLU);
-  for (int s = 0; s < 2; ++s) {
-    // Y = X Q_L^T (n x N), G_fresh = 1 - Q_R Y, in the path precision
-    const T* qr = reinterpret_cast<const T*>(QR[s]);
-    const T* ql = reinterpret_cast<const T*>(QL[s]);
-    if constexpr (!std::is_same<T, double>::value) {
-      T* qrt = x.QRt();
-      T* qlt = x.QLt();
-      PQMC_FOR_2D(k, 0, n[s], i, 0, N) {
-        qrt[(long)k * N + i] = (T)QR[s][(long)k * N + i];
-        qlt[(long)k * N + i] = (T)QL[s][(long)k * N + i];
-      }
-      qr = qrt;
-      ql = qlt;
-      __syncthreads();
-    }
-    cta_gemm<T>(n[s], N, n[s], O[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
-    __syncthreads();
-    EpiFresh<T> epi{x.G(s), ld, &dmax};
-    cta_gemm<T>(N, N, n[s], qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
-    const double l_tot = c.Rlog[(b * 2 + s) * 2 + 0] + la[s] + c.Llog[(b * 2 + s) * 2 + 0];
-    const double s_tot = c.Rlog[(b * 2 + s) * 2 + 1] * sg[s] * c.Llog[(b * 2 + s) * 2 + 1];
-    if (threadIdx.x == 0) {
-      sh.logw_spin[s] = l_tot;
-      sh.sign_spin[s] = s_tot;
-    }
-    sign_total *= s_tot;
-    __syncthreads();
-  }
-  x.mark(kPhAssemble);
-  const double dm = cta_max((double)dmax, sh.red);
-  if (threadIdx.x == 0) {
-    const double dmax = dm;
-    if (!isfinite(dmax)) sh.err |= kErrNaN;
-    if (record) {
-      sh.dGmax = fmax(sh.dGmax, dmax);
-      c.dG[c.st->n_dG % kDGHistory] = dmax;
-      c.st->n_dG++;
-    }
-    c.st->sign_stack = sign_total;
-  }
-  __syncthreads();
-}
-
-// Wick estimates on the fresh G at the middle slice: E/site for Eq. (2),
-// docc/site, kinetic/site, with the weight sign and the running sign.
-template <typename T>
-__device__ void measure(Cta<T>& x) {
-  const ChainDesc& c = x.c;
-  Smem<T>& sh = x.sh;
-  const int N = c.N, ld = c.ld;
-  double ek = 0.0, dc = 0.0;
-  PQMC_FOR_2D(i, 0, N, j, 0, N) {
-    const double k = c.K64[(long)i * N + j];
-    if (k != 0.0) {
-      for (int s = 0; s < 2; ++s) ek += k * ((i == j ? 1.0 : 0.0) - (double)x.G(s)[(long)j * ld + i]);
-    }
-  }
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
-    dc += (1.0 - (double)x.G(0)[(long)i * ld + i]) * (1.0 - (double)x.G(1)[(long)i * ld + i]);
-  ek = cta_sum(ek, sh.red);
-  dc = cta_sum(dc, sh.red);
-  if (threadIdx.x == 0) {
-    const int m = c.st->n_meas;
-    const double rec[kRecord] = {sh.sign_spin[0] * sh.sign_spin[1], (ek + c.U * dc) / N, dc / N, ek / N,
-                                 sh.sign_running};
-    for (int k = 0; k < kRecord; ++k) {
-      if (m < c.max_meas) c.meas[(long)m * kRecord + k] = rec[k];
-      c.last[k] = rec[k];
-    }
-    c.st->n_meas = m + 1;
-  }
-  __syncthreads();
-}
-
-// --------------------------------------------------------------------------
-// sweeps
-
-template <typename T>
-__device__ void sweep_up(Cta<T>& x, uint32_t sweep, bool do_measure) {
-  const ChainDesc& c = x.c;
-  for (int tau = 0; tau <= c.Ltau + 1; ++tau) {
-    update_slice(x, tau, sweep);
-    wrap(x, tau, +1);
-    x.mark(kPhWrap);
-    if (tau <= c.Ltau && tau % c.n_stab == 0) {
-      const int b = tau / c.n_stab;
-      push_R(x, b);
-      refresh(x, b, true);
-      x.mark(kPhRefresh);
-      if (do_measure && tau == c.Ltau / 2) measure(x);
-      x.mark(kPhMeasure);
-    }
-  }
-}
-
-template <typename T>
-__device__ void sweep_down(Cta<T>& x, uint32_t sweep, bool do_measure) {
-  const ChainDesc& c = x.c;
-  for (int tau = c.Ltau + 1; tau >= 0; --tau) {
-    wrap(x, tau, -1);
-    x.mark(kPhWrap);
-    update_slice(x, tau, sweep);
-    const int t1 = tau - 1;
-    if (t1 >= 0 && t1 % c.n_stab == 0) {
-      const int b = t1 / c.n_stab;
-      push_L(x, b);
-      refresh(x, b, true);
-      x.mark(kPhRefresh);
-      if (do_measure && t1 == c.Ltau / 2) measure(x);
-      x.mark(kPhMeasure);
-    }
-  }
-}
-
-template <typename T>
-__device__ void load_state(Cta<T>& x) {
-  if (threadIdx.x == 0) {
-    const ChainState& st = *x.c.st;
-    x.sh.sign_running = st.sign_running;
-    x.sh.dGmax = st.max_dG;
-    x.sh.n_prop = st.n_prop;
-    x.sh.n_acc = st.n_acc;
-    x.sh.acc_pos = st.acc_pos;
-    x.sh.err = 0;
-    x.sh.staged = -1;
-    x.sh.sign_spin[0] = st.logw[0][1];
-    x.sh.sign_spin[1] = st.logw[1][1];
-    x.sh.logw_spin[0] = st.logw[0][0];
-    x.sh.logw_spin[1] = st.logw[1][0];
-  }
-  if (threadIdx.x < 8) {
-    const int k = threadIdx.x >> 2, s = (threadIdx.x >> 1) & 1, si = threadIdx.x & 1;
-    x.sh.vtab[k][s][si] = x.c.vexp[k][s][si];
-    x.sh.vt[k][s][si] = (T)x.c.vexp[k][s][si];
-    x.sh.vti[k][s][si] = (T)(1.0 / x.c.vexp[k][s][si]);
-  }
-  if (threadIdx.x < kPhases) x.sh.cyc[threadIdx.x] = 0;
-  if (threadIdx.x == 0) x.sh.t_mark = clock64();
-  __syncthreads();
-}
-
-template <typename T>
-__device__ void store_state(Cta<T>& x, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ChainState& st = *x.c.st;
-    st.sign_running = x.sh.sign_running;
-    st.max_dG = x.sh.dGmax;
-    st.n_prop = x.sh.n_prop;
-    st.n_acc = x.sh.n_acc;
-    st.acc_pos = x.sh.acc_pos;
-    st.err |= x.sh.err;
-    for (int s = 0; s < 2; ++s) {
-      st.logw[s][0] = x.sh.logw_spin[s];
-      st.logw[s][1] = x.sh.sign_spin[s];
-    }
-    for (int p = 0; p < kPhases; ++p) st.cycles[p] += x.sh.cyc[p];
-    if (x.sh.err) atomicOr(err, x.sh.err);
-  }
-}
-
-// Place G and the scratch: in shared memory after the fixed part when the
-// chain's footprint fits in res_bytes (G is copied in), else in global memory.
-template <typename T>
-__device__ Cta<T> make_cta(const ChainDesc& cg, unsigned char* smem_raw, size_t res_bytes, uint64_t seed) {
-  Smem<T>& sh = *reinterpret_cast<Smem<T>*>(smem_raw);
-  // the descriptor is read all through the sweep: keep a shared-memory copy
-  {
-    const int words = (int)(sizeof(ChainDesc) / sizeof(int));
-    const int* src = reinterpret_cast<const int*>(&cg);
-    int* dst = reinterpret_cast<int*>(&sh.desc);
-    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
-    __syncthreads();
-  }
-  const ChainDesc& c = sh.desc;
-  const int ts = (int)sizeof(T);
-  const ScratchLayout L = scratch_layout(c.N, c.ld, c.nmax, ts);
-  const bool res = resident_bytes(c.N, c.ld, c.nmax, ts) <= res_bytes;
-  unsigned char* dyn = smem_raw + al16(sizeof(Smem<T>));
-  T* Gp = res ? reinterpret_cast<T*>(dyn) : reinterpret_cast<T*>(c.G);
-  unsigned char* scr = res ? dyn + al16(2 * (size_t)c.N * c.ld * ts) : reinterpret_cast<unsigned char*>(c.scratch);
-  FlipBuf<T>* fb = reinterpret_cast<FlipBuf<T>*>(res ? scr + L.fb : dyn);
-  Cta<T> x{c, sh, seed, Gp, scr, L, res, fb};
-  if (res) {
-    const T* g = reinterpret_cast<const T*>(c.G);
-    for (long e = threadIdx.x; e < 2L * c.N * c.ld; e += blockDim.x) Gp[e] = g[e];
-  }
-  return x;
-}
-
-template <typename T>
-__device__ void write_back(Cta<T>& x) {
-  __syncthreads();
-  if (x.resident) {
-    T* g = reinterpret_cast<T*>(x.c.G);
-    for (long e = threadIdx.x; e < 2L * x.c.N * x.c.ld; e += blockDim.x) g[e] = x.Gp[e];
-  }
-  __syncthreads();
-}
-
-template <typename T, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) init_kernel(const ChainDesc* chains, int chain0, uint64_t seed,
-                                                          size_t res_bytes, int* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cta<T> x = make_cta<T>(chains[chain0 + blockIdx.x], smem_raw, res_bytes, seed);
-  Smem<T>& sh = x.sh;
-  load_state(x);
-  const ChainDesc& c = x.c;
-  for (int b = c.nb; b >= 0; --b) push_L(x, b);
-  push_R(x, 0);
-  refresh(x, 0, false);
-  if (threadIdx.x == 0) sh.sign_running = sh.sign_spin[0] * sh.sign_spin[1];
-  __syncthreads();
-  wrap(x, 0, -1);
-  write_back(x);
-  store_state(x, err);
-}
-
-template <typename T, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) sweep_kernel(const ChainDesc* chains, uint64_t seed,
-                                                       const uint32_t* sweep_ctr, int n_sweeps, int do_measure,
-                                                       size_t res_bytes, int* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (chains[blockIdx.x].st->err) return;
-  const uint32_t sweep0 = *sweep_ctr;
-  Cta<T> x = make_cta<T>(chains[blockIdx.x], smem_raw, res_bytes, seed);
-  Smem<T>& sh = x.sh;
-  load_state(x);
-  const long long t_start = clock64();
-  for (int k = 0; k < n_sweeps; ++k) {
-    const uint32_t sw = sweep0 + (uint32_t)k;
-    if ((sw & 1u) == 0) sweep_up(x, sw, do_measure != 0);
-    else sweep_down(x, sw, do_measure != 0);
-    __syncthreads();
-    if (sh.err) break;
-  }
-  if (threadIdx.x == 0) sh.cyc[kPhTotal] += clock64() - t_start;
-  write_back(x);
-  store_state(x, err);
-}
 
 // --------------------------------------------------------------------------
 // host launch wrappers (called from api.cpp)
@@ -1220,68 +23,34 @@ size_t smem_resident_cap(int prec, int tpb, int boost) {
   return per_cta > fixed ? per_cta - fixed : 0;
 }
 
-template <typename T>
-static size_t dyn_smem(size_t res) {
-  const size_t fbb = flipbuf_bytes((int)sizeof(T));
-  return al16(sizeof(Smem<T>)) + (res > fbb ? res : fbb);
-}
-
-template <typename T, int TPB, int MINB>
-static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res, int* d_err,
-                                 cudaStream_t stream) {
-  const size_t sm = dyn_smem<T>(res);
-  cudaError_t e = cudaFuncSetAttribute(init_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  init_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, chain0, seed, res, d_err);
-  return cudaGetLastError();
-}
-
 // The sweep index lives in device memory (sweep_ctr) and is advanced by a
 // one-thread kernel after each sweep launch, so that the pair can be captured
 // once in a CUDA graph and replayed.
 __global__ void advance_sweep_kernel(uint32_t* sweep_ctr, int n) { *sweep_ctr += (uint32_t)n; }
 
-template <typename T, int TPB, int MINB>
-static cudaError_t prepare_sweep_t(size_t res) {
-  return cudaFuncSetAttribute(sweep_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)dyn_smem<T>(res));
-}
-
-template <typename T, int TPB, int MINB>
-static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr, int n_sweeps,
-                                  int measure, size_t res, int* d_err, cudaStream_t stream) {
-  sweep_kernel<T, TPB, MINB><<<n, TPB, dyn_smem<T>(res), stream>>>(d_chains, seed, sweep_ctr, n_sweeps, measure, res,
-                                                                   d_err);
-  advance_sweep_kernel<<<1, 1, 0, stream>>>(sweep_ctr, n_sweeps);
+cudaError_t launch_advance(uint32_t* sweep_ctr, int n, cudaStream_t stream) {
+  advance_sweep_kernel<<<1, 1, 0, stream>>>(sweep_ctr, n);
   return cudaGetLastError();
 }
 
-#define PQMC_DISPATCH(CALL, ...)                                                        \
-  do {                                                                                  \
-    if (prec == 0) {                                                                    \
-      if (tpb == 64) return CALL<double, 64, 4>(__VA_ARGS__);                           \
-      if (tpb == 128) return CALL<double, 128, 2>(__VA_ARGS__);                         \
-      return CALL<double, 256, 1>(__VA_ARGS__);                                         \
-    }                                                                                   \
-    if (boost) {                                                                        \
-      if (tpb == 64) return CALL<float, 64, 16>(__VA_ARGS__);                           \
-      return CALL<float, 128, 8>(__VA_ARGS__);                                          \
-    }                                                                                   \
-    if (tpb == 64) return CALL<float, 64, 8>(__VA_ARGS__);                              \
-    if (tpb == 128) return CALL<float, 128, 4>(__VA_ARGS__);                            \
-    return CALL<float, 256, 2>(__VA_ARGS__);                                            \
-  } while (0)
-
 cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
                         size_t res, int* d_err, cudaStream_t stream) {
-  PQMC_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream);
+  if (prec == 0) return launch_init_f64(tpb, d_chains, chain0, n, seed, res, d_err, stream);
+  if (boost) return launch_init_f32_dense(tpb, d_chains, chain0, n, seed, res, d_err, stream);
+  return launch_init_f32(tpb, d_chains, chain0, n, seed, res, d_err, stream);
 }
 
-cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res) { PQMC_DISPATCH(prepare_sweep_t, res); }
+cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res) {
+  if (prec == 0) return prepare_sweep_f64(tpb, res);
+  if (boost) return prepare_sweep_f32_dense(tpb, res);
+  return prepare_sweep_f32(tpb, res);
+}
 
 cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains, int n, uint64_t seed,
                          uint32_t* sweep_ctr, int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {
-  PQMC_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
+  if (prec == 0) return launch_sweep_f64(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
+  if (boost) return launch_sweep_f32_dense(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
+  return launch_sweep_f32(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
 }
 
 // --------------------------------------------------------------------------

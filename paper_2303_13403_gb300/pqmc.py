@@ -39,10 +39,15 @@ class Opts(C.Structure):
                 ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int), ("dense_chains", C.c_int)]
 
 
+# columns of a measurement record: sign of the weight, E/site, docc/site,
+# kinetic/site, running sign, S_AFM
+RECORD = 6
+
+
 class Obs(C.Structure):
     _fields_ = [("E", C.c_double), ("E_err", C.c_double), ("docc", C.c_double), ("docc_err", C.c_double),
                 ("sign", C.c_double), ("sign_err", C.c_double), ("accept", C.c_double), ("max_dG", C.c_double),
-                ("n_meas", C.c_long)]
+                ("n_meas", C.c_long), ("s_afm", C.c_double), ("s_afm_err", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -175,15 +180,15 @@ class Context:
         return dict(zip(("N", "N_up", "N_dn", "Ltau", "n_stab", "delay_k"), list(d)))
 
     def measurements(self, chain=0, cap=1 << 16):
-        out = np.zeros((cap, 5))
+        out = np.zeros((cap, RECORD))
         n = C.c_long(cap)
         _check(load().pqmc_get_measurements(self._h, chain, _dptr(out), C.byref(n)), self._h)
         return out[: n.value]
 
     def last_records(self, out=None):
-        """Latest record of every chain (n_chains x 5), one device-to-host copy."""
+        """Latest record of every chain (n_chains x RECORD), one device-to-host copy."""
         if out is None:
-            out = np.zeros((self.n_chains, 5))
+            out = np.zeros((self.n_chains, RECORD))
         _check(load().pqmc_get_last_records(self._h, _dptr(out)), self._h)
         return out
 

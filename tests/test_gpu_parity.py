@@ -88,6 +88,7 @@ def test_accept_sequence_10_sweeps_plain_18():
     assert len(rec) == 10
     assert np.allclose(rec[:, 1], [m.energy for m in ch.measurements], rtol=1e-10, atol=0)
     assert np.allclose(rec[:, 2], [m.docc for m in ch.measurements], rtol=1e-10, atol=0)
+    assert np.allclose(rec[:, 5], [m.s_afm for m in ch.measurements], rtol=1e-10, atol=0)
     assert np.all(rec[:, 0] == 1.0) and np.all(rec[:, 4] == 1.0)
     assert np.array_equal(ctx.fields(), ch.fields)
     obs = ctx.measure(0)
@@ -112,6 +113,7 @@ def test_sweep_parity(spec, n_sweeps, n_stab):
         assert rel_err(ctx.green(0, s), ch.G[sg]) < 1e-10
     rec = ctx.measurements()
     assert np.allclose(rec[:, 1], [m.energy for m in ch.measurements], rtol=1e-10, atol=1e-12)
+    assert np.allclose(rec[:, 5], [m.s_afm for m in ch.measurements], rtol=1e-10, atol=1e-14)
     assert np.array_equal(rec[:, 0], [m.sign for m in ch.measurements])
     assert np.array_equal(rec[:, 4], [m.sign_running for m in ch.measurements])
 
@@ -174,8 +176,9 @@ def test_fp32_stabilisation_error_distribution():
 
 @pytest.mark.parametrize("prec", [pqmc.FP64, pqmc.FP32, pqmc.BF16X3])
 def test_mc_energy_within_3sigma_of_exact(prec):
-    """64 independent chains on the 8-site cluster; the pooled estimate of E and
-    docc agrees with the exact Trotterised projection (Fock space) within 3 sigma."""
+    """64 independent chains on the 8-site cluster; the pooled estimates of E,
+    docc and S_AFM agree with the exact Trotterised projection (Fock space)
+    within 3 sigma."""
     spec = SMALL
     ctx = pqmc.Context([spec] * 64, prec=prec, seed=21, n_stab=5 if prec == pqmc.FP64 else 2)
     ctx.sweep(10, measure=False)
@@ -183,10 +186,11 @@ def test_mc_energy_within_3sigma_of_exact(prec):
     obs = ctx.measure(-1)
     m = opq.Model(oracle_params(spec, n_stab=5))
     c = ed.Cluster(m.K, 4, 4, spec.U)
-    Ex, Dx = c.trotter_projection(m.P[1], m.P[-1], spec.g, spec.dtau, m.Ltau)
+    Ex, Dx, Sx = c.trotter_observables(m.P[1], m.P[-1], spec.g, spec.dtau, m.Ltau, m.eps)
     assert obs["n_meas"] == 64 * 60
     assert abs(obs["E"] - Ex / 8) < 3 * obs["E_err"], (obs, Ex / 8)
     assert abs(obs["docc"] - Dx / 8) < 3 * obs["docc_err"], (obs, Dx / 8)
+    assert abs(obs["s_afm"] - Sx) < 3 * obs["s_afm_err"], (obs, Sx)
     assert obs["E_err"] < 0.01
     assert obs["sign"] == 1.0
 

@@ -97,3 +97,22 @@ def test_host_model_matches_oracle(lib, spec):
         Po = m.P[sigma]
         assert np.allclose(P @ P.T, Po @ Po.T, atol=1e-9)
         assert np.isclose(gap, m.gap[sigma], rtol=1e-8)
+
+
+def test_variational_quadratic_minimum():
+    """The refinement of the grid minimum recovers the stationary point of an
+    exact paraboloid, and declines when the neighbourhood holds no minimum."""
+    from paper_2303_13403_gb300 import variational
+    gv = np.array(variational.G_VALUES)
+    mv = np.array(variational.M_VALUES)
+    G, M = np.meshgrid(gv, mv, indexing="ij")
+    E = -0.9 + 0.3 * (G - 0.57) ** 2 + 0.1 * (G - 0.57) * (M - 0.08) + 2.0 * (M - 0.08) ** 2
+    err = np.full_like(E, 1e-3)
+    s = variational.summarise(gv, mv, E, err)
+    assert s["grid_argmin"]["g"] == 0.6 and s["grid_argmin"]["M_N"] == 0.09
+    f = s["fit_min"]
+    assert abs(f["g"] - 0.57) < 1e-9 and abs(f["M_N"] - 0.08) < 1e-9 and abs(f["E"] + 0.9) < 1e-12
+    assert variational.quadratic_minimum(gv, mv, -E, err, (5, 5)) is None
+    specs = variational.grid_specs(3.5, 6)
+    assert len(specs) == 121 and all(sp.two_theta == 0.0 and sp.n_sites == 72 for sp in specs)
+    assert specs[12].g == 0.1 and specs[12].M_N == 0.03

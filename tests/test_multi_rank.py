@@ -15,7 +15,8 @@ def synthetic_records(chain, n=40):
     s = np.where(rng.random(n) < 0.9, 1.0, -1.0)
     E = -0.8 + 0.05 * rng.standard_normal(n)
     D = 0.12 + 0.01 * rng.standard_normal(n)
-    return np.column_stack([s, E, D, E, s])
+    A = 0.03 + 0.005 * rng.standard_normal(n)
+    return np.column_stack([s, E, D, E, s, A])
 
 
 def _free_port():
@@ -54,8 +55,8 @@ def test_two_rank_reduction_equals_single_process():
     assert [r[1] for r in res] == [0, 5]                      # distinct Philox chain indices
     ref = distributed.pooled_estimate(distributed.chain_sums([synthetic_records(c) for c in range(10)]))
     for _, _, est, shape in res:
-        assert shape == (10, 4)
-        for k in ("E", "E_err", "docc", "docc_err", "sign", "sign_err"):
+        assert shape == (10, 5)
+        for k in ("E", "E_err", "docc", "docc_err", "s_afm", "s_afm_err", "sign", "sign_err"):
             assert np.isclose(est[k], ref[k], rtol=1e-12, atol=0), k
 
 
@@ -65,4 +66,5 @@ def test_pooled_estimate_matches_direct_ratio():
     allr = np.concatenate(recs)
     assert np.isclose(est["E"], np.sum(allr[:, 0] * allr[:, 1]) / np.sum(allr[:, 0]), rtol=1e-14)
     assert np.isclose(est["sign"], np.mean(allr[:, 0]), rtol=1e-14)
+    assert np.isclose(est["s_afm"], np.sum(allr[:, 0] * allr[:, 5]) / np.sum(allr[:, 0]), rtol=1e-14)
     assert est["n_meas"] == 240 and est["E_err"] > 0
