@@ -99,12 +99,12 @@ struct ScratchLayout {
   size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, o, y, qrt, qlt, laux, total;
 };
 
-PQMC_HDI size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 // Per-block buffers of the flip phase (kBlock x kBlock blocks of both spins,
 // uniforms, accepted sites); the layout is FlipBuf<T> in sweep.cu.
-PQMC_HDI size_t flipbuf_bytes(int tsize) {
-  return al16(4 * (size_t)kBlock * (kBlock + 1) * tsize + 2 * (size_t)kBlock * tsize + (size_t)kBlock * (8 + 4 + 4 + 4));
+PQMC_HDI constexpr size_t flipbuf_bytes(int tsize) {
+  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 4 * (size_t)kBlock * tsize + (size_t)kBlock * 4);
 }
 
 PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {

@@ -308,14 +308,13 @@ __device__ void path_gemm(const ChainDesc& c, int M, int Nn, int K, const T* A, 
 // Buffers of one flip block (lives in shared memory, see make_cta).
 template <typename T>
 struct FlipBuf {
-  T Gb[2][kBlock][kBlock + 1];      // diagonal block of current G, both spins
   T Tu[2][kBlock][kBlock + 1];      // 1 + (1 - G_SS) Gamma, inverted in place, then M
   T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
-  double u[kBlock];                 // Metropolis uniforms of the block
-  float uf[kBlock];                 // the same rounded down to 24 bits (FP32 decisions)
+  T rs[2][kBlock];                  // ratio R_sigma of each proposal of the block
   int sites[kBlock];                // block index of each accepted flip
-  int fl[kBlock];                   // fields of the block
 };
+static_assert(sizeof(FlipBuf<double>) <= flipbuf_bytes(8) && sizeof(FlipBuf<float>) <= flipbuf_bytes(4),
+              "flip buffer layout");
 
 template <typename T>
 struct Smem {
@@ -413,10 +412,13 @@ struct Cta {
 // only on the new fields; the pivots of the a x a inverse are the accepted
 // ratios, so Gauss-Jordan without pivoting follows the sequential process.
 
+// The Metropolis uniform u = m 2^-53 of the 53-bit Philox mantissa m, in the
+// decision precision: exact in FP64; in FP32 rounded down to 24 bits, so
+// u < |R| is decided in FP32 on both sides of a comparison with the oracle.
 template <typename T>
-__device__ __forceinline__ bool metropolis_accept(double u, float uf, T R) {
-  if constexpr (std::is_same<T, double>::value) return u < fabs(R);
-  else return uf < fabsf(R);
+__device__ __forceinline__ T uniform_of(uint64_t m53) {
+  if constexpr (std::is_same<T, double>::value) return (double)m53 * 0x1.0p-53;
+  else return (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;
 }
 
 template <typename T>
@@ -434,64 +436,67 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
 
   for (int i0 = 0; i0 < N; i0 += kBlock) {
     const int nbk = min(kBlock, N - i0);
-    for (int e = threadIdx.x; e < 2 * kBlock * kBlock; e += blockDim.x) {
-      const int s = e / (kBlock * kBlock), r = (e / kBlock) % kBlock, q = e % kBlock;
-      fb.Gb[s][r][q] = (r < nbk && q < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + q] : T(0);
-    }
-    if (threadIdx.x < kBlock) {
-      const int j = threadIdx.x;
-      if (j < nbk) {
-        const U4 w = philox4x32_10((uint32_t)(i0 + j), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
+    if (warp < 2) {
+      // warp s (spin s): lane q holds column q of the spin's diagonal block in
+      // registers; the two warps exchange the spin ratios through shared
+      // memory once per proposal and take the same decision
+      const int s = warp;
+      T gs[kBlock];
+      const bool colq = lane < nbk;
+#pragma unroll
+      for (int r = 0; r < kBlock; ++r) gs[r] = (colq && r < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + lane] : T(0);
+      // lane j: uniform (in the decision precision) and field of site i0 + j
+      T uj = T(2);
+      int flj = 1;
+      if (colq) {
+        const U4 w = philox4x32_10((uint32_t)(i0 + lane), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
                                    (uint32_t)(x.seed >> 32));
-        const uint64_t m53 = ((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11);
-        fb.u[j] = (double)m53 * 0x1.0p-53;
-        fb.uf[j] = (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;   // the same uniform rounded down to 24 bits
-      } else {
-        fb.u[j] = 2.0;
-        fb.uf[j] = 2.0f;
+        uj = uniform_of<T>(((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11));
+        flj = (int)f[i0 + lane];
       }
-      fb.fl[j] = j < nbk ? (int)f[i0 + j] : 1;
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-      int a = 0;
-      for (int j = 0; j < nbk; ++j) {
-        const int si = fb.fl[j] > 0 ? 0 : 1;
-        const T d0 = dl[0][si], d1 = dl[1][si];
-        const T r0 = T(1) + d0 * (T(1) - fb.Gb[0][j][j]);
-        const T r1 = T(1) + d1 * (T(1) - fb.Gb[1][j][j]);
-        const T R = r0 * r1;
-        const bool acc = metropolis_accept<T>(fb.u[j], fb.uf[j], R);
-        if (lane == 0) {
-          if (!isfinite(R)) sh.err |= kErrNaN;
-          if (sh.acc_pos < c.acc_cap) c.acc_log[sh.acc_pos] = acc ? 1 : 0;
-          sh.acc_pos++;
-          sh.n_prop++;
-        }
-        if (!acc) continue;
-        const T c0 = d0 / r0, c1 = d1 / r1;
-        if (lane > j && lane < nbk) {
-          const T y0 = c0 * fb.Gb[0][j][lane], y1 = c1 * fb.Gb[1][j][lane];
-#pragma unroll 4
-          for (int r = j + 1; r < nbk; ++r) {
-            fb.Gb[0][r][lane] = fma(fb.Gb[0][r][j], y0, fb.Gb[0][r][lane]);
-            fb.Gb[1][r][lane] = fma(fb.Gb[1][r][j], y1, fb.Gb[1][r][lane]);
+      int a = 0, bad = 0, nneg = 0;
+      const long long pos0 = sh.acc_pos;
+#pragma unroll
+      for (int j = 0; j < kBlock; ++j) {
+        if (j < nbk) {
+          const int si = __shfl_sync(0xffffffffu, flj, j) > 0 ? 0 : 1;
+          const T ds = dl[s][si];
+          const T rs = T(1) + ds * (T(1) - __shfl_sync(0xffffffffu, gs[j], j));
+          if (lane == 0) fb.rs[s][j] = rs;
+          asm volatile("bar.sync 1, 64;" ::: "memory");
+          const T R = fb.rs[0][j] * fb.rs[1][j];
+          const bool acc = __shfl_sync(0xffffffffu, (int)(uj < (R < T(0) ? -R : R)), j) != 0;
+          if (s == 0 && lane == 0) {
+            if (!isfinite(R)) bad = 1;
+            if (pos0 + j < c.acc_cap) c.acc_log[pos0 + j] = acc ? 1 : 0;
+          }
+          if (acc) {
+            // G_rq += c G_rj G_jq for future rows r > j and columns q > j
+            const T y = lane > j ? (ds / rs) * gs[j] : T(0);
+#pragma unroll
+            for (int r = j + 1; r < kBlock; ++r) gs[r] = fma(__shfl_sync(0xffffffffu, gs[r], j), y, gs[r]);
+            if (lane == j) {
+              flj = -flj;
+              if (s == 0) f[i0 + j] = (int8_t)flj;
+            }
+            if (s == 0 && lane == 0) {
+              fb.sites[a] = j;
+              fb.cl[0][a] = ds;
+              fb.cl[1][a] = dl[1][si];
+              nneg += R < T(0) ? 1 : 0;
+            }
+            ++a;
           }
         }
-        if (lane == 0) {
-          fb.sites[a] = j;
-          fb.cl[0][a] = d0;
-          fb.cl[1][a] = d1;
-          fb.fl[j] = -fb.fl[j];
-          f[i0 + j] = (int8_t)fb.fl[j];
-          sh.sign_running *= (R < T(0)) ? -1.0 : 1.0;
-          sh.n_acc++;
-        }
-        ++a;
-        __syncwarp();
       }
-      if (lane == 0) sh.na = a;
+      if (s == 0 && lane == 0) {
+        sh.na = a;
+        sh.acc_pos = pos0 + nbk;
+        sh.n_prop += nbk;
+        sh.n_acc += a;
+        if (nneg & 1) sh.sign_running = -sh.sign_running;
+        if (bad) sh.err |= kErrNaN;
+      }
     }
     __syncthreads();
     x.mark(kPhFlip);
