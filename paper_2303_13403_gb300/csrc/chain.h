@@ -92,11 +92,12 @@ namespace pqmc {
 //             and the per-block flip buffers
 //   stack   : M64 (N x n, FP64, column-major), then a region holding the two
 //             path-precision product buffers Mt, Mt2 (N x n, T, row-major)
-//             and later the FP64 Q of the QR; Householder betas / R_jj
+//             and later the FP64 Q of the QR; Householder betas / R_jj;
+//             the Gram matrix and pivots of the Cholesky QR
 //   refresh : O (n x n, FP64, both spins, inverted in place), Y (n x ld, T), Q_R and Q_L in the
 //             path precision (N x n, T); LU pivots / multipliers
 struct ScratchLayout {
-  size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, o, y, qrt, qlt, laux, total;
+  size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, total;
 };
 
 PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -123,7 +124,8 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   const size_t two_mt = 2 * al16(Nn * tsize);
   const size_t mtq_sz = two_mt > al16(Nn * 8) ? two_mt : al16(Nn * 8);
   L.qaux = L.mtq + mtq_sz;
-  size_t stack = L.qaux + al16((3 * (size_t)n + (size_t)kQRParts * n) * 8);
+  L.chol = L.qaux + al16((3 * (size_t)n + (size_t)kQRParts * n) * 8);
+  size_t stack = L.chol + al16(((size_t)n * n + 3 * (size_t)n) * 8);
   L.o = 0;                                   // O for spin 0, then spin 1 (inverted in place)
   L.y = 2 * al16((size_t)n * n * 8);
   L.qrt = L.y + al16((size_t)n * ld * tsize);

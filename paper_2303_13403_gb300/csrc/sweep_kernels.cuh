@@ -329,6 +329,7 @@ struct Smem {
   int na;                           // accepted flips in the block
   int piv;
   int nswap[2];
+  int chol_bad;
   int staged;                       // slice held in fr, or -1
   double sign_running;
   double sign_spin[2];
@@ -362,6 +363,7 @@ struct Cta {
   __device__ double* qalpha() const { return qbeta() + c.nmax; }
   __device__ double* qw() const { return qbeta() + 2 * c.nmax; }
   __device__ double* qpart() const { return qbeta() + 3 * c.nmax; }
+  __device__ double* chol() const { return reinterpret_cast<double*>(scr + L.chol); }
   __device__ double* Ob(int s) const {
     return reinterpret_cast<double*>(scr + L.o + s * al16((size_t)c.nmax * c.nmax * 8));
   }
@@ -710,6 +712,126 @@ __device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, do
   x.mark(kPhQRForm);
 }
 
+// Upper triangle (2 x 2 tiles on or above the diagonal) of C = M^T M for the
+// column-major N x n matrix M (ld N); C row-major n x n.
+static __device__ void gram_upper_f64(int n, int N, const double* M, double* C) {
+  const int tn = (n + 1) >> 1;
+  for (int t = threadIdx.x; t < tn * tn; t += blockDim.x) {
+    const int ti = t / tn, tj = t - ti * tn;
+    if (tj < ti) continue;
+    const int i0 = ti << 1, j0 = tj << 1;
+    const double* a0 = M + (long)i0 * N;
+    const double* a1 = M + (long)min(i0 + 1, n - 1) * N;
+    const double* b0 = M + (long)j0 * N;
+    const double* b1 = M + (long)min(j0 + 1, n - 1) * N;
+    double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      const double x0 = a0[k], x1 = a1[k], y0 = b0[k], y1 = b1[k];
+      c00 = fma(x0, y0, c00);
+      c01 = fma(x0, y1, c01);
+      c10 = fma(x1, y0, c10);
+      c11 = fma(x1, y1, c11);
+    }
+    C[(long)i0 * n + j0] = c00;
+    if (j0 + 1 < n) C[(long)i0 * n + j0 + 1] = c01;
+    if (i0 + 1 < n) {
+      C[(long)(i0 + 1) * n + j0] = c10;
+      if (j0 + 1 < n) C[(long)(i0 + 1) * n + j0 + 1] = c11;
+    }
+  }
+}
+
+// Cholesky QR of the column-major N x n matrix M (ld N), used for the stack
+// blocks of the reduced-precision paths: C = M^T M = R^T R, Q = M R^{-1}
+// (Stathopoulos & Wu, SIAM J. Sci. Comput. 23 (2002); the loss of
+// orthogonality grows like eps cond(M)^2, Yamamoto et al., ETNA 44 (2015)).
+// With two slices per stabilisation cond(M) stays near 1e2, and it needs n
+// CTA barriers per factor and per solve instead of the Householder QR's
+// sequence of reflector, dot and update phases.  Every FP64 step runs over a
+// flat or 2D index of the whole CTA.  Returns false, with M unchanged, when a
+// pivot falls below 1e-12 of its original diagonal entry (cond(M) above about
+// 1e6); the caller then takes the Householder QR.  R has a positive diagonal,
+// so only log|det R| = (1/2) sum_k log(pivot_k) is returned.
+template <typename T>
+__device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs) {
+  Smem<T>& sh = x.sh;
+  double* C = x.chol();                 // n x n row-major (upper part): Gram, then factored in place
+  double* d0 = C + (long)n * n;         // original diagonal
+  double* ip = d0 + n;                  // 1 / pivot
+  double* isq = ip + n;                 // 1 / sqrt(pivot)
+  gram_upper_f64(n, N, M, C);
+  if (threadIdx.x == 0) sh.chol_bad = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) d0[k] = C[(long)k * n + k];
+  if (threadIdx.x == 0) ip[0] = 1.0 / C[0];
+  __syncthreads();
+  // right-looking factorisation with the rows left unscaled: after step k,
+  // C_ij (i, j > k) holds the Schur complement, C_kk the pivot p_k, and row k
+  // is scaled to U_kj = C_kj / p_k (= R_kj / R_kk) one step later
+  for (int k = 0; k < n; ++k) {
+    const double p = C[(long)k * n + k];
+    if (!(p > 1e-12 * d0[k])) {          // same value in every thread: uniform exit
+      if (threadIdx.x == 0) sh.chol_bad = 1;
+      break;
+    }
+    const double ipk = ip[k];
+    if (k > 0) {
+      const double ipm = ip[k - 1];
+      for (int j = k + (int)threadIdx.x; j < n; j += blockDim.x) C[(long)(k - 1) * n + j] *= ipm;
+    }
+    // Schur update of the upper triangle: warp per row i, lanes over j >= i
+    for (int i = k + 1 + (int)(threadIdx.x >> 5); i < n; i += (int)(blockDim.x >> 5)) {
+      const double li = C[(long)k * n + i] * ipk;
+      for (int j = i + (int)(threadIdx.x & 31); j < n; j += 32)
+        C[(long)i * n + j] = fma(-li, C[(long)k * n + j], C[(long)i * n + j]);
+      if (i == k + 1 && (threadIdx.x & 31) == 0) ip[i] = 1.0 / C[(long)i * n + i];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (sh.chol_bad) return false;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) isq[k] = rsqrt(C[(long)k * n + k]);
+  __syncthreads();
+  x.mark(kPhQR);
+  // Q = M R^{-1}, right-looking over the columns of M: q_k = m_k / R_kk,
+  // m_j -= m_k U_kj for j > k (m_k is read only in its own step)
+  {
+    // flat index over (column jj >= k, row i) stepped incrementally, so every
+    // FP64 warp instruction carries full warps
+    const int step = (int)blockDim.x, sq = step / N, sr = step - sq * N;
+    const int t0 = (int)threadIdx.x / N, r0 = (int)threadIdx.x - t0 * N;
+    for (int k = 0; k < n; ++k) {
+      const double sk = isq[k];
+      int jj = k + t0, i = r0;
+      while (jj < n) {
+        const double mk = M[(long)k * N + i];
+        if (jj == k) Q[(long)k * N + i] = mk * sk;
+        else M[(long)jj * N + i] = fma(-mk, C[(long)k * n + jj], M[(long)jj * N + i]);
+        i += sr;
+        jj += sq;
+        if (i >= N) { i -= N; ++jj; }
+      }
+      __syncthreads();
+    }
+  }
+  // log|det R|
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+      double la = 0.0;
+      for (int k = lane; k < n; k += 32) la += log(C[(long)k * n + k]);
+      la = warp_sum(la);
+      if (lane == 0) sh.red[0] = 0.5 * la;
+    }
+    __syncthreads();
+    logabs = sh.red[0];
+    __syncthreads();
+  }
+  x.mark(kPhQRForm);
+  return true;
+}
+
 // Invert O_s (n_s x n_s, row-major) in place for both spins at once by
 // Gauss-Jordan elimination with partial pivoting (Golub & Van Loan, section
 // 3.2): warp s finds the pivot of spin s, swaps the rows, scales the pivot row
@@ -768,18 +890,21 @@ __device__ void gj_invert2(Cta<T>& x, const int n[2], double* O[2], double logab
     // eliminate column j from every other row of both spins: one FMA per
     // element over a flat index (full warps on the FP64 pipe); the pivot
     // column takes -f_i / pivot through the same FMA with a zero addend
-    {
-      const int e0 = j < n[0] ? n[0] * n[0] : 0;
-      const int e1 = j < n[1] ? n[1] * n[1] : 0;
-      for (int e = threadIdx.x; e < e0 + e1; e += blockDim.x) {
-        const int s = e < e0 ? 0 : 1;
-        const int ns = n[s], loc = e - (s ? e0 : 0);
-        const int i = loc / ns, col = loc - i * ns;
-        double* A = O[s];
-        const double fi = x.lmul(s)[i];
+    for (int s = 0; s < 2; ++s) {
+      const int ns = n[s];
+      if (j >= ns) continue;
+      double* A = O[s];
+      const double* fl = x.lmul(s);
+      // flat (row, column) index stepped incrementally
+      const int step = (int)blockDim.x, sq = step / ns, sr = step - sq * ns;
+      int i = (int)threadIdx.x / ns, col = (int)threadIdx.x - i * ns;
+      while (i < ns) {
         const double add = col == j ? 0.0 : A[(long)i * ns + col];
-        const double r = fma(-fi, A[(long)j * ns + col], add);
+        const double r = fma(-fl[i], A[(long)j * ns + col], add);
         if (i != j) A[(long)i * ns + col] = r;
+        col += sr;
+        i += sq;
+        if (col >= ns) { col -= ns; ++i; }
       }
     }
     __syncthreads();
@@ -877,9 +1002,10 @@ __device__ void push_R(Cta<T>& x, int b) {
       PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
       __syncthreads();
     }
-    double la, sg;
+    double la, sg = 1.0;
     x.mark(kPhStack);
-    qr_householder(x, N, n, M, x.Q64(), la, sg);
+    if (std::is_same<T, double>::value || !qr_cholesky(x, N, n, M, x.Q64(), la))
+      qr_householder(x, N, n, M, x.Q64(), la, sg);
     copy_block(x.Q64(), stack_block(x, c.Rst, b, s), N * n);
     x.mark(kPhQR);
     if (threadIdx.x == 0) {
@@ -922,9 +1048,10 @@ __device__ void push_L(Cta<T>& x, int b) {
       PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
       __syncthreads();
     }
-    double la, sg;
+    double la, sg = 1.0;
     x.mark(kPhStack);
-    qr_householder(x, N, n, M, x.Q64(), la, sg);
+    if (std::is_same<T, double>::value || !qr_cholesky(x, N, n, M, x.Q64(), la))
+      qr_householder(x, N, n, M, x.Q64(), la, sg);
     copy_block(x.Q64(), stack_block(x, c.Lst, b, s), N * n);
     x.mark(kPhQR);
     if (threadIdx.x == 0) {
