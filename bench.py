@@ -41,12 +41,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3", "fp64"])
-    ap.add_argument("--chains", type=int, default=608, help="chains per GPU (4 per SM)")
+    ap.add_argument("--chains", type=int, default=608, help="chains per GPU (two waves of 2 chains per SM)")
     ap.add_argument("--two-theta", type=float, default=8.0)
     ap.add_argument("--n-stab", type=int, default=0, help="0: 2 for fp32 and bf16x3, 10 for fp64")
     ap.add_argument("--beside-steps", type=int, default=3, help="steps of the other precisions timed beside (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cta-threads", type=int, default=0, help="threads per chain CTA (0: library default)")
     return ap.parse_args()
 
 
@@ -187,7 +188,7 @@ def run_ours(a):
 
     def timed(name, n_stab_, steps, warmup, clocks=False):
         ctx = pqmc.Context(specs, prec=PRECS[name], seed=1, n_stab=n_stab_, chain_offset=rank * a.chains,
-                           max_meas=warmup + steps + 1, stream=stream.cuda_stream)
+                           max_meas=warmup + steps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads)
         for _ in range(warmup):
             ctx.sweep(1, measure=False)
         ctx.synchronize()
@@ -266,7 +267,7 @@ def run_ours(a):
     barrier()
     t0 = time.perf_counter()
     ctx = pqmc.Context(specs, prec=PRECS[head], seed=2, n_stab=n_stab, chain_offset=rank * a.chains,
-                       max_meas=a.steps + 1, stream=stream.cuda_stream)
+                       max_meas=a.steps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads)
     h2d = ctx.device_bytes()
     rec = np.zeros((a.chains, pqmc.RECORD))
     d2h = 0

@@ -118,7 +118,7 @@ typedef struct {
     int max_meas;           /* capacity of per-sweep measurement records per chain (0 = 4096) */
     void* stream;           /* cudaStream_t to run on, or NULL for a library-owned stream */
     int cta_threads;        /* threads of the CTA that runs one chain: 64, 128 or 256; 0 picks
-                               64 for FP64 and 128 otherwise. Smaller CTAs put more chains
+                               64 for FP64 and 256 otherwise. Smaller CTAs put more chains
                                on one SM (FP64: 256/cta_threads per SM, others twice that) */
     int dense_chains;       /* reduced paths only: kernels built for twice as many chains per SM
                                (fewer registers per thread); needs cta_threads 64 or 128 */

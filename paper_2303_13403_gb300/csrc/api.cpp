@@ -251,8 +251,9 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   }
   ctx->off_last = take((size_t)n * kRecord * 8);
   // default CTA size (measured on GB300 at 72 sites): the FP64 path packs 4
-  // chains of 64 threads per SM, the reduced paths 4 chains of 128 threads
-  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : 128);
+  // chains of 64 threads per SM; the reduced paths 2 chains of 256 threads,
+  // whose G and scratch then fit in shared memory
+  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : 256);
   {
     ctx->boost = (ctx->prec != PQMC_FP64 && o.dense_chains) ? 1 : 0;
     const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb, ctx->boost);

@@ -81,3 +81,15 @@ def test_doped_square_signs_consistent():
         rec = ctx.measurements(c)
         assert set(np.unique(rec[:, 0])) <= {-1.0, 1.0}
         assert np.array_equal(rec[:, 0], rec[:, 4])
+
+
+def test_theta_convergence_study_runs():
+    """The Theta-convergence study (three trial states, uneven projection
+    lengths in one context) on the 8-site cluster: every group yields a finite
+    energy and S_AFM in range, with sign +1 at half filling."""
+    from paper_2303_13403_gb300 import convergence
+    r = convergence.run(L=2, Us=(4.0,), two_thetas=(0.4, 1.6), chains=4, n_warm=2, n_meas=10)
+    assert len(r["rows"]) == 3 * 2
+    for row in r["rows"]:
+        assert np.isfinite(row["E"]) and np.isfinite(row["s_afm"]) and row["sign"] == 1.0
+        assert -1.5 < row["E"] < 0.5 and 0.0 < row["s_afm"] <= 0.25
