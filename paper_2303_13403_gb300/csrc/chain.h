@@ -95,9 +95,10 @@ namespace pqmc {
 //             and later the FP64 Q of the QR; Householder betas / R_jj;
 //             the Gram matrix and pivots of the Cholesky QR
 //   refresh : O (n x n, FP64, both spins, inverted in place), Y (n x ld, T), Q_R and Q_L in the
-//             path precision (N x n, T); LU pivots / multipliers
+//             path precision (N x n, T); LU pivots / multipliers; O^{-1} in
+//             the path precision (n x n, T)
 struct ScratchLayout {
-  size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, total;
+  size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, ot, total;
 };
 
 PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -125,13 +126,14 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   const size_t mtq_sz = two_mt > al16(Nn * 8) ? two_mt : al16(Nn * 8);
   L.qaux = L.mtq + mtq_sz;
   L.chol = L.qaux + al16((3 * (size_t)n + (size_t)kQRParts * n) * 8);
-  size_t stack = L.chol + al16(((size_t)n * n + 3 * (size_t)n) * 8);
+  size_t stack = L.chol + al16((2 * (size_t)n * n + 3 * (size_t)n) * 8);
   L.o = 0;                                   // O for spin 0, then spin 1 (inverted in place)
   L.y = 2 * al16((size_t)n * n * 8);
   L.qrt = L.y + al16((size_t)n * ld * tsize);
   L.qlt = L.qrt + al16(Nn * tsize);
   L.laux = L.qlt + al16(Nn * tsize);
-  size_t refresh = L.laux + al16(2 * 3 * (size_t)n * 8);
+  L.ot = L.laux + al16(2 * 3 * (size_t)n * 8);
+  size_t refresh = L.ot + al16((size_t)n * n * tsize);
   size_t t = wrap;
   if (flush > t) t = flush;
   if (stack > t) t = stack;

@@ -370,6 +370,7 @@ struct Cta {
   __device__ T* Yb() const { return reinterpret_cast<T*>(scr + L.y); }
   __device__ T* QRt() const { return reinterpret_cast<T*>(scr + L.qrt); }
   __device__ T* QLt() const { return reinterpret_cast<T*>(scr + L.qlt); }
+  __device__ T* Ot() const { return reinterpret_cast<T*>(scr + L.ot); }
   __device__ double* pval(int s) const { return reinterpret_cast<double*>(scr + L.laux) + s * 3 * c.nmax; }
   __device__ double* pinv(int s) const { return pval(s) + c.nmax; }
   __device__ double* lmul(int s) const { return pval(s) + 2 * c.nmax; }
@@ -756,8 +757,9 @@ static __device__ void gram_upper_f64(int n, int N, const double* M, double* C) 
 template <typename T>
 __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs) {
   Smem<T>& sh = x.sh;
-  double* C = x.chol();                 // n x n row-major (upper part): Gram, then factored in place
-  double* d0 = C + (long)n * n;         // original diagonal
+  double* C = x.chol();                 // n x n row-major (upper part): Gram, then Schur complements
+  double* U = C + (long)n * n;          // n x n row-major (upper part): U_kj = R_kj / R_kk
+  double* d0 = U + (long)n * n;         // original diagonal
   double* ip = d0 + n;                  // 1 / pivot
   double* isq = ip + n;                 // 1 / sqrt(pivot)
   gram_upper_f64(n, N, M, C);
@@ -766,9 +768,11 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
   for (int k = threadIdx.x; k < n; k += blockDim.x) d0[k] = C[(long)k * n + k];
   if (threadIdx.x == 0) ip[0] = 1.0 / C[0];
   __syncthreads();
-  // right-looking factorisation with the rows left unscaled: after step k,
-  // C_ij (i, j > k) holds the Schur complement, C_kk the pivot p_k, and row k
-  // is scaled to U_kj = C_kj / p_k (= R_kj / R_kk) one step later
+  // right-looking factorisation: step k scales row k into U (U_kj = C_kj / p_k)
+  // and then updates the trailing block, C_ij -= C_ki U_kj (i, j > k; the
+  // part below the diagonal is updated too, so the flat loop keeps the warps
+  // full, and never read)
+  const int step = (int)blockDim.x;
   for (int k = 0; k < n; ++k) {
     const double p = C[(long)k * n + k];
     if (!(p > 1e-12 * d0[k])) {          // same value in every thread: uniform exit
@@ -776,16 +780,22 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
       break;
     }
     const double ipk = ip[k];
-    if (k > 0) {
-      const double ipm = ip[k - 1];
-      for (int j = k + (int)threadIdx.x; j < n; j += blockDim.x) C[(long)(k - 1) * n + j] *= ipm;
-    }
-    // Schur update of the upper triangle: warp per row i, lanes over j >= i
-    for (int i = k + 1 + (int)(threadIdx.x >> 5); i < n; i += (int)(blockDim.x >> 5)) {
-      const double li = C[(long)k * n + i] * ipk;
-      for (int j = i + (int)(threadIdx.x & 31); j < n; j += 32)
-        C[(long)i * n + j] = fma(-li, C[(long)k * n + j], C[(long)i * n + j]);
-      if (i == k + 1 && (threadIdx.x & 31) == 0) ip[i] = 1.0 / C[(long)i * n + i];
+    for (int j = k + 1 + (int)threadIdx.x; j < n; j += step) U[(long)k * n + j] = C[(long)k * n + j] * ipk;
+    __syncthreads();
+    const int m = n - k - 1;
+    if (m > 0) {
+      const int sq = step / m, sr = step - sq * m;
+      int i = (int)threadIdx.x / m, j = (int)threadIdx.x - i * m;
+      const double* Ck = C + (long)k * n + k + 1;
+      const double* Uk = U + (long)k * n + k + 1;
+      double* Cb = C + (long)(k + 1) * n + k + 1;
+      while (i < m) {
+        Cb[(long)i * n + j] = fma(-Ck[i], Uk[j], Cb[(long)i * n + j]);
+        if (i == 0 && j == 0) ip[k + 1] = 1.0 / Cb[0];
+        j += sr;
+        i += sq;
+        if (j >= m) { j -= m; ++i; }
+      }
     }
     __syncthreads();
   }
@@ -794,20 +804,20 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
   for (int k = threadIdx.x; k < n; k += blockDim.x) isq[k] = rsqrt(C[(long)k * n + k]);
   __syncthreads();
   x.mark(kPhQR);
-  // Q = M R^{-1}, right-looking over the columns of M: q_k = m_k / R_kk,
-  // m_j -= m_k U_kj for j > k (m_k is read only in its own step)
   {
-    // flat index over (column jj >= k, row i) stepped incrementally, so every
-    // FP64 warp instruction carries full warps
-    const int step = (int)blockDim.x, sq = step / N, sr = step - sq * N;
+    // Q = M R^{-1}, right-looking over the columns of M: q_k = m_k / R_kk,
+    // m_j -= m_k U_kj for j > k (m_k is read only in its own step); a flat
+    // (column jj >= k, row i) index stepped incrementally keeps the warps full
+    const int sq = step / N, sr = step - sq * N;
     const int t0 = (int)threadIdx.x / N, r0 = (int)threadIdx.x - t0 * N;
     for (int k = 0; k < n; ++k) {
       const double sk = isq[k];
+      const double* Uk = U + (long)k * n;
       int jj = k + t0, i = r0;
       while (jj < n) {
         const double mk = M[(long)k * N + i];
         if (jj == k) Q[(long)k * N + i] = mk * sk;
-        else M[(long)jj * N + i] = fma(-mk, C[(long)k * n + jj], M[(long)jj * N + i]);
+        else M[(long)jj * N + i] = fma(-mk, Uk[jj], M[(long)jj * N + i]);
         i += sr;
         jj += sq;
         if (i >= N) { i -= N; ++jj; }
@@ -1114,7 +1124,15 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
       ql = qlt;
       __syncthreads();
     }
-    cta_gemm<T>(n[s], N, n[s], O[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
+    if constexpr (std::is_same<T, double>::value) {
+      cta_gemm<T>(n[s], N, n[s], O[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
+    } else {
+      // O^{-1} to the path precision once, then a path-precision product
+      T* ot = x.Ot();
+      for (int e = threadIdx.x; e < n[s] * n[s]; e += blockDim.x) ot[e] = (T)O[s][e];
+      __syncthreads();
+      cta_gemm<T>(n[s], N, n[s], ot, n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
+    }
     __syncthreads();
     EpiFresh<T> epi{x.G(s), ld, &dmax};
     cta_gemm<T>(N, N, n[s], qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
