@@ -148,19 +148,33 @@ def fp32_peak_tflops(sm_mhz):
 
 
 # ---------------------------------------------------------------- our arm
-def sweep_flops(N, n, Ltau, n_stab, acc):
+def sweep_flops(N, n, Ltau, n_stab, acc, prec):
     """Algorithmic flops per sweep per chain, both spins: (path-precision, FP64).
 
     Path precision, per interaction slice per spin: wrap 4 N^3, delayed-update
     flush 2 acc N^3, stack slice products 2 N^2 n.  FP64, per stabilisation per
-    spin: Householder QR 2 n^2 (N - n/3), forming Q 2 n^2 (N - n/3),
-    Q_L^T Q_R 2 n^2 N, Gauss-Jordan inverse 2 n^3."""
+    spin: QR of the N x n stack block -- Householder with Q formed (FP64 path)
+    4 n^2 (N - n/3), Cholesky QR (reduced paths) N n (n + 1) for the Gram
+    matrix's upper triangle + n^3/3 for the factor + N n^2 for Q = M R^{-1} --
+    then Q_L^T Q_R 2 n^2 N and the Gauss-Jordan inverse 2 n^3."""
     path = 2 * Ltau * (4 * N ** 3 + 2 * acc * N ** 3 + 2 * N * N * n)
-    stab = (Ltau // n_stab + 1) * 2 * (4 * n * n * (N - n / 3) + 2 * n * n * N + 2 * n ** 3)
+    if prec == "fp64":
+        qr = 4 * n * n * (N - n / 3)
+    else:
+        qr = N * n * (n + 1) + n ** 3 / 3 + N * n * n
+    stab = (Ltau // n_stab + 1) * 2 * (qr + 2 * n * n * N + 2 * n ** 3)
     return path, stab
 
 
-FP64_PEAK_TFLOPS = 1.2   # measured on this pool's GB300 (FMA throughput probe; DGEMM 1.06)
+# FP64 peak from the unit counts and the clock: 152 SMs x 2 FP64 FMA lanes per
+# clock x 2 flop x 2070 MHz = 1.26 TFLOP/s, the part's nominal 1.25 TFLOP/s
+# (an FMA-throughput probe on this pool measured 1.2 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
+
+# DRAM bytes (read + write) per chain and sweep of the sweep kernel, FP32 path,
+# 72 sites, 2 Theta = 8, 256-thread CTAs: one ncu capture of 304 chains
+# (profiles/sweep_kernel_gutz72_ncu.md), 1053.4 MB per launch / 304.
+DRAM_BYTES_PER_CHAIN_SWEEP = {"fp32": 1053.35e6 / 304}
 
 
 def run_ours(a):
@@ -285,12 +299,18 @@ def run_ours(a):
     # roofline of the sweep kernel (one launch per step): the binding pipe is
     # FP64 for every path (the stabilisation in the reduced paths, everything
     # in the FP64 path)
-    path_f, stab_f = sweep_flops(N, N // 2, Ltau, n_stab, res["accept"])
+    path_f, stab_f = sweep_flops(N, N // 2, Ltau, n_stab, res["accept"], head)
     launch_s = ms / 1e3 / a.steps
     fp64_f = stab_f + (path_f if head == "fp64" else 0.0)
     fp64_achieved = fp64_f * a.chains / launch_s / 1e12
     fp32_achieved = (path_f * a.chains / launch_s / 1e12) if head != "fp64" else 0.0
     fp32_peak = fp32_peak_tflops(2070.0)
+    # time the two pipes need at their peaks, as a fraction of the launch
+    bound_s = fp64_f * a.chains / (FP64_PEAK_TFLOPS * 1e12) + (
+        path_f * a.chains / (fp32_peak * 1e12) if head != "fp64" else 0.0)
+    traffic = (DRAM_BYTES_PER_CHAIN_SWEEP[head] * a.chains
+               if head in DRAM_BYTES_PER_CHAIN_SWEEP and N == 72 and Ltau == 80 and a.cta_threads in (0, 256)
+               else None)
     result = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -308,9 +328,10 @@ def run_ours(a):
         "E_per_site": res["E_per_site"], "E_err": res["E_err"], "accept": res["accept"],
         "dG_per_stabilisation": res["dG_per_stabilisation"],
         "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": fp64_achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sweep_kernel",
+                     "frac": fp64_achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "sweep_kernel",
                      "pipe": "fp64",
-                     "peak_source": "FP64 FMA throughput measured on this pool's GB300 (1.2 TFLOP/s)",
+                     "peak_source": "152 SMs x 2 FP64 FMA lanes x 2 flop x 2070 MHz (nominal 1.25 TFLOP/s)",
+                     "two_pipe_bound_frac": bound_s / launch_s,
                      "fp32_pipe": {"achieved": fp32_achieved, "peak": fp32_peak,
                                    "frac": fp32_achieved / fp32_peak,
                                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}},
