@@ -20,7 +20,9 @@
  *    Ltau+1 carry the Gutzwiller fields; 1..Ltau the Hubbard fields.
  *    B_tau = e^{-dtau K} e^{V(s_tau)} (interaction slices),
  *    B_tau = e^{V(s_tau)} (Gutzwiller slices).
- *  - Fields are int8 in {-1,+1}, laid out [tau][i], (Ltau+2) x N per chain.
+ *  - Fields are int8 in {-1,+1}, laid out [tau][i], (Ltau+2) x N per chain
+ *    ((Ltau+2) x 3N/2 bond fields for PQMC_HONEYCOMB_TV, where "site" in the
+ *    Philox counter is the bond index and G has one species, spin 0).
  *  - Green's functions are G_ij = <c_i c_j^+>, row-major N x N, spin 0 = up,
  *    spin 1 = down.
  *  - One sweep is one directional pass that proposes every field once;
@@ -74,13 +76,27 @@ typedef enum {
                            FP32 accumulation */
 } pqmc_precision;
 
-typedef enum { PQMC_HONEYCOMB = 0, PQMC_SQUARE = 1 } pqmc_lattice_kind;
+typedef enum { PQMC_HONEYCOMB = 0, PQMC_SQUARE = 1, PQMC_HONEYCOMB_TV = 2 } pqmc_lattice_kind;
 
 /* Lattice: honeycomb Lx x Ly unit cells (N = 2 Lx Ly; site 2(x + Lx y) + sub,
  * A(x,y) bonds to B(x,y), B(x-1,y), B(x,y-1)) or square Lx x Ly (N = Lx Ly,
  * site x + Lx y, hopping -t to nearest and -tp to next-nearest neighbours).
  * Periodic in both directions; a bond that wraps onto an existing one adds
- * its amplitude again. */
+ * its amplitude again.
+ *
+ * PQMC_HONEYCOMB_TV selects the spinless t-V model of the paper's second
+ * model (Eq. (4)) on the same honeycomb lattice: one fermion species,
+ * H = -t sum_<ij> (c^+_i c_j + h.c.) + V sum_<ij> (n_i - 1/2)(n_j - 1/2), with
+ * the bond Gutzwiller trial of Eq. (5).  Its fields sit on the 3N/2 bonds
+ * (bond 3 c + k of cell c = x + Lx y joins A(x,y) to B(x,y), B(x-1,y),
+ * B(x,y-1) for k = 0, 1, 2), each decoupled in the density-difference
+ * channel exp(kappa s (n_i - n_j)); a slice proposes its bonds class by class
+ * (k = 0, 1, 2), cells ascending, and the weight is one determinant, whose
+ * sign can be negative.  In its chain spec U is V, trial.g the bond
+ * Gutzwiller parameter, trial.M_N the CDW field Delta_C of
+ * H_C = H_0 + Delta_C sum_i eps_i n_i (raised to 1e-4 when smaller, or to
+ * trial.tiebreak when that is >= 0), trial.N_up the number of fermions (< 0:
+ * N/2) and trial.N_dn must be 0 or < 0. */
 typedef struct {
     int kind;           /* pqmc_lattice_kind */
     int Lx, Ly;
@@ -130,7 +146,10 @@ typedef struct {
  * AFM structure factor of the Fig. 2 comparison, taken as its z component
  * (1/N^2) sum_ij eps_i eps_j <S^z_i S^z_j>, S^z_i = (n_i,up - n_i,dn)/2 and
  * eps_i = +1 on sublattice A, -1 on B (the paper defers the definition to its
- * supplement). */
+ * supplement).  For PQMC_HONEYCOMB_TV chains E is the energy per site of
+ * Eq. (4), docc holds the interaction energy per site
+ * V sum_<ij> <(n_i - 1/2)(n_j - 1/2)> / N, and s_afm the CDW structure factor
+ * (1/N^2) sum_ij eps_i eps_j <(n_i - 1/2)(n_j - 1/2)>. */
 typedef struct {
     double E, E_err;
     double docc, docc_err;
@@ -184,7 +203,7 @@ pqmc_status pqmc_get_measurements(pqmc_ctx* ctx, int chain, double* out, long* n
  * for a chain that has no record yet). Synchronises first. */
 pqmc_status pqmc_get_last_records(pqmc_ctx* ctx, double* out);
 
-/* Replace the fields of one chain ((Ltau+2) x N int8, values +-1) and rebuild its
+/* Replace the fields of one chain ((Ltau+2) x fields-per-slice int8, values +-1) and rebuild its
  * stacks and G as at initialisation. Allowed only when an even number of
  * sweeps has been run (the next sweep goes up). */
 pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields);
@@ -214,7 +233,8 @@ pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n)
  * eliminations, column restore and log-determinant). */
 pqmc_status pqmc_get_phase_cycles(pqmc_ctx* ctx, int chain, long long* out);
 
-/* Sizes of one chain: out[0..5] = (N, N_up, N_dn, Ltau, n_stab, delay_k). */
+/* Sizes of one chain: out[0..6] = (N, N_up, N_dn, Ltau, n_stab, delay_k,
+ * fields per slice: N, or 3N/2 bonds for PQMC_HONEYCOMB_TV). */
 pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out);
 
 /* Number of chains in the context, or -1 for NULL. */
@@ -261,7 +281,8 @@ pqmc_status pqmc_host_eigh(int n, const double* A, double* w, double* V);
  * pqmc_get_weight compute for one chain: the left stack and G at tau = -1
  * for the given fields, with the same kernel.
  *
- *   spec     host pointer, one chain (validated as in pqmc_init_batch)
+ *   spec     host pointer, one chain of a Hubbard lattice (validated as in
+ *            pqmc_init_batch; PQMC_HONEYCOMB_TV is rejected)
  *   n_stab   slices between QR stabilisations (Ltau/2 must be a multiple)
  *   d_fields device pointer, (Ltau+2) x N int8 fields in {-1,+1}, read only
  *   d_G      device pointer, output, 2 x N x N FP64: G_up then G_dn, row-major

@@ -35,9 +35,10 @@ thread_local std::string g_init_error;
 
 struct HostChain {
   pqmc_chain_spec spec;
-  int N, ld, nup, ndn, nmax, Ltau, nb;
+  int N, ld, nup, ndn, nmax, Ltau, nb, nfld;
   size_t off_fields, off_G, off_Rst, off_Lst, off_Rlog, off_Llog, off_meas, off_dG,
-      off_acc, off_state, off_P, off_scratch, off_expKm, off_expKp, off_expKm64, off_K64, off_eps;
+      off_acc, off_state, off_P, off_scratch, off_expKm, off_expKp, off_expKm64, off_K64, off_eps, off_bonds,
+      off_sbonds;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -81,12 +82,37 @@ pqmc_status cuda_fail(pqmc_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, PQMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-int n_sites(const pqmc_lattice& l) { return l.kind == PQMC_HONEYCOMB ? 2 * l.Lx * l.Ly : l.Lx * l.Ly; }
+int n_sites(const pqmc_lattice& l) { return l.kind == PQMC_SQUARE ? l.Lx * l.Ly : 2 * l.Lx * l.Ly; }
+bool is_tv(const pqmc_chain_spec& s) { return s.lattice.kind == PQMC_HONEYCOMB_TV; }
 
 // model tables shared by chains with the same lattice and dtau
 struct ModelTables {
   std::vector<double> K, eps, w, V, expKm, expKp;
+  std::vector<int> bond_ends, site_bonds;   // t-V only
 };
+
+// Bonds of the honeycomb lattice for the t-V model: bond 3 c + k of cell
+// c = x + Lx y joins A(x, y) to B(x, y), B(x-1, y), B(x, y-1) (k = 0, 1, 2);
+// site_bonds lists the three bonds of every site.
+void tv_bonds(int Lx, int Ly, std::vector<int>& ends, std::vector<int>& site_bonds) {
+  const int nc = Lx * Ly;
+  auto site = [&](int x, int y, int sub) { return 2 * (((x % Lx) + Lx) % Lx + Lx * (((y % Ly) + Ly) % Ly)) + sub; };
+  ends.assign(6 * nc, 0);
+  site_bonds.assign(6 * nc, 0);
+  std::vector<int> fill(2 * nc, 0);
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) {
+      const int c = x + Lx * y, a = site(x, y, 0);
+      const int bs[3] = {site(x, y, 1), site(x - 1, y, 1), site(x, y - 1, 1)};
+      for (int k = 0; k < 3; ++k) {
+        const int b = 3 * c + k;
+        ends[2 * b] = a;
+        ends[2 * b + 1] = bs[k];
+        site_bonds[3 * a + fill[a]++] = b;
+        site_bonds[3 * bs[k] + fill[bs[k]]++] = b;
+      }
+    }
+}
 
 std::string lattice_key(const pqmc_chain_spec& s) {
   char buf[256];
@@ -102,12 +128,18 @@ void set_init_error(const std::string& msg) { g_init_error = msg; }
 
 pqmc_status check_spec(const pqmc_chain_spec& s, int n_stab, std::string& why) {
   const auto& l = s.lattice;
-  if (l.kind != PQMC_HONEYCOMB && l.kind != PQMC_SQUARE) { why = "unknown lattice kind"; return PQMC_EINVAL; }
+  if (l.kind != PQMC_HONEYCOMB && l.kind != PQMC_SQUARE && l.kind != PQMC_HONEYCOMB_TV) {
+    why = "unknown lattice kind"; return PQMC_EINVAL;
+  }
   if (l.Lx < 1 || l.Ly < 1 || l.Lx > 64 || l.Ly > 64) { why = "lattice extent out of range"; return PQMC_EINVAL; }
   const int N = n_sites(l);
   if (N > kMaxN) { why = "more than 1024 sites"; return PQMC_EINVAL; }
   const int nup = s.trial.N_up < 0 ? N / 2 : s.trial.N_up;
-  const int ndn = s.trial.N_dn < 0 ? N / 2 : s.trial.N_dn;
+  if (l.kind == PQMC_HONEYCOMB_TV) {
+    if (s.trial.N_dn > 0) { why = "t-V chains have one species: N_dn must be 0 or < 0"; return PQMC_EINVAL; }
+    if (nup < 1 || nup > N) { why = "N_up must be in 1..N"; return PQMC_EINVAL; }
+  }
+  const int ndn = l.kind == PQMC_HONEYCOMB_TV ? nup : (s.trial.N_dn < 0 ? N / 2 : s.trial.N_dn);
   if (nup < 1 || ndn < 1 || nup > N || ndn > N) { why = "N_sigma must be in 1..N"; return PQMC_EINVAL; }
   if (nup > kMaxSigma || ndn > kMaxSigma) { why = "N_sigma above 512"; return PQMC_EINVAL; }
   if (!(s.dtau > 0) || !(s.two_theta >= 0) || !std::isfinite(s.U) || s.U < 0) {
@@ -195,15 +227,18 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     h.N = n_sites(s.lattice);
     h.ld = (int)align_up(h.N, 4);
     h.nup = s.trial.N_up < 0 ? h.N / 2 : s.trial.N_up;
-    h.ndn = s.trial.N_dn < 0 ? h.N / 2 : s.trial.N_dn;
+    h.ndn = is_tv(s) ? 0 : (s.trial.N_dn < 0 ? h.N / 2 : s.trial.N_dn);
     h.nmax = std::max(h.nup, h.ndn);
+    h.nfld = is_tv(s) ? 3 * h.N / 2 : h.N;
     h.Ltau = (int)std::lround(s.two_theta / s.dtau);
     h.nb = h.Ltau / o.n_stab;
     const std::string key = lattice_key(s);
     if (!models.count(key)) {
       ModelTables mt;
-      Lattice lat{s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t, s.lattice.tp};
+      Lattice lat{is_tv(s) ? (int)PQMC_HONEYCOMB : s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t,
+                  s.lattice.tp};
       build_hopping(lat, mt.K, mt.eps);
+      if (is_tv(s)) tv_bonds(s.lattice.Lx, s.lattice.Ly, mt.bond_ends, mt.site_bonds);
       if (!sym_eig(h.N, mt.K, mt.w, mt.V)) { delete ctx; return fail(nullptr, PQMC_EINVAL, "eigensolver failed on K"); }
       expm_from_eig(h.N, mt.w, mt.V, -s.dtau, mt.expKm);
       expm_from_eig(h.N, mt.w, mt.V, +s.dtau, mt.expKp);
@@ -214,11 +249,14 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
       take((size_t)h.N * h.N * 8);
       take((size_t)h.N * h.N * 8);
       take((size_t)h.N * 8);
+      take((size_t)h.N * 3 * 4);             // bond ends (3N/2 x 2 int)
+      take((size_t)h.N * 3 * 4);             // site bonds (N x 3 int)
       model_off[key] = o1;
     }
     const ModelTables& mt = models[key];
-    Lattice lat{s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t, s.lattice.tp};
-    for (int sp = 0; sp < 2; ++sp) {
+    Lattice lat{is_tv(s) ? (int)PQMC_HONEYCOMB : s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t,
+                s.lattice.tp};
+    for (int sp = 0; sp < (is_tv(s) ? 1 : 2); ++sp) {
       double gap = 0;
       if (!trial_orbitals(lat, mt.K, mt.eps, s.trial.M_N, s.trial.tiebreak, sp == 0 ? 1 : -1,
                           sp == 0 ? h.nup : h.ndn, trials[c].P[sp], gap)) {
@@ -234,9 +272,11 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     h.off_expKm64 = h.off_expKp + align_up((size_t)h.N * h.ld * ctx->tsize, 256);
     h.off_K64 = h.off_expKm64 + align_up((size_t)h.N * h.N * 8, 256);
     h.off_eps = h.off_K64 + align_up((size_t)h.N * h.N * 8, 256);
+    h.off_bonds = h.off_eps + align_up((size_t)h.N * 8, 256);
+    h.off_sbonds = h.off_bonds + align_up((size_t)h.N * 3 * 4, 256);
     const size_t Gbytes = 2ull * h.N * h.ld * ctx->tsize;
     const size_t blk = (size_t)h.N * h.nmax * 8;
-    h.off_fields = take((size_t)(h.Ltau + 2) * h.N);
+    h.off_fields = take((size_t)(h.Ltau + 2) * h.nfld);
     h.off_G = take(Gbytes);
     h.off_P = take(2 * blk);
     h.off_Rst = take((size_t)(h.nb + 1) * 2 * blk);
@@ -284,6 +324,10 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
       put<double>(A, h.off_expKm64, mt.expKm, h.N, h.N, h.N);
       put<double>(A, h.off_K64, mt.K, h.N, h.N, h.N);
       memcpy(A.data() + h.off_eps, mt.eps.data(), (size_t)h.N * 8);
+      if (is_tv(s)) {
+        memcpy(A.data() + h.off_bonds, mt.bond_ends.data(), mt.bond_ends.size() * 4);
+        memcpy(A.data() + h.off_sbonds, mt.site_bonds.data(), mt.site_bonds.size() * 4);
+      }
       written[key] = true;
     }
     // P_sigma column-major (ld N) in blocks of N x nmax
@@ -296,7 +340,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     int8_t* F = reinterpret_cast<int8_t*>(A.data() + h.off_fields);
     const uint32_t chain_index = (uint32_t)(o.chain_offset + c);
     for (int t = 0; t < h.Ltau + 2; ++t)
-      for (int i = 0; i < h.N; ++i) F[(size_t)t * h.N + i] = (int8_t)initial_field(o.seed, chain_index, t, i);
+      for (int i = 0; i < h.nfld; ++i) F[(size_t)t * h.nfld + i] = (int8_t)initial_field(o.seed, chain_index, t, i);
     double* last = reinterpret_cast<double*>(A.data() + ctx->off_last) + (size_t)c * kRecord;
     for (int k = 0; k < kRecord; ++k) last[k] = NAN;
     ChainState st{};
@@ -330,8 +374,12 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.Ltau = h.Ltau; d.nb = h.nb; d.n_stab = o.n_stab; d.kb = o.delay_k;
     d.chain_index = (uint32_t)(o.chain_offset + c);
     d.tc = ctx->prec == PQMC_BF16X3 ? 1 : 0;
+    d.tv = is_tv(s) ? 1 : 0;
+    d.nfld = h.nfld;
     d.U = s.U;
     const double kap[2] = {hs_coupling(s.dtau * s.U), hs_coupling(s.trial.g)};
+    for (int k = 0; k < 2; ++k)
+      for (int m = -3; m <= 3; ++m) d.vtv[k][m + 3] = std::exp(kap[k] * m);
     for (int k = 0; k < 2; ++k)
       for (int sp = 0; sp < 2; ++sp)
         for (int si = 0; si < 2; ++si) {
@@ -347,6 +395,8 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.expKm64 = reinterpret_cast<const double*>(b + h.off_expKm64);
     d.K64 = reinterpret_cast<const double*>(b + h.off_K64);
     d.eps = reinterpret_cast<const double*>(b + h.off_eps);
+    d.bond_ends = reinterpret_cast<const int*>(b + h.off_bonds);
+    d.site_bonds = reinterpret_cast<const int*>(b + h.off_sbonds);
     d.P = reinterpret_cast<const double*>(b + h.off_P);
     d.Rst = reinterpret_cast<double*>(b + h.off_Rst);
     d.Lst = reinterpret_cast<double*>(b + h.off_Lst);
@@ -570,7 +620,7 @@ pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields) {
   if (ctx->sweep_index & 1u) return fail(ctx, PQMC_EINVAL, "set_fields needs an even number of sweeps done");
   if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
   const HostChain& h = ctx->chains[chain];
-  const size_t nf = (size_t)(h.Ltau + 2) * h.N;
+  const size_t nf = (size_t)(h.Ltau + 2) * h.nfld;
   for (size_t i = 0; i < nf; ++i)
     if (fields[i] != 1 && fields[i] != -1) return fail(ctx, PQMC_EINVAL, "fields must be +1 or -1");
   cudaError_t e = cudaMemcpyAsync(ctx->desc[chain].fields, fields, nf, cudaMemcpyHostToDevice, ctx->stream);
@@ -588,7 +638,7 @@ pqmc_status pqmc_get_fields(pqmc_ctx* ctx, int chain, int8_t* fields) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
   const HostChain& h = ctx->chains[chain];
-  e = cudaMemcpy(fields, ctx->desc[chain].fields, (size_t)(h.Ltau + 2) * h.N, cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(fields, ctx->desc[chain].fields, (size_t)(h.Ltau + 2) * h.nfld, cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "fields copy");
 }
 
@@ -666,6 +716,7 @@ pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out) {
   if (!chain_ok(ctx, chain) || !out) return PQMC_EINVAL;
   const HostChain& h = ctx->chains[chain];
   out[0] = h.N; out[1] = h.nup; out[2] = h.ndn; out[3] = h.Ltau; out[4] = ctx->opts.n_stab; out[5] = ctx->opts.delay_k;
+  out[6] = h.nfld;
   return PQMC_OK;
 }
 

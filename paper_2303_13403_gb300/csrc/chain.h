@@ -47,16 +47,22 @@ struct ChainDesc {
   int Ltau, nb, n_stab, kb;
   uint32_t chain_index;
   int tc;                  // 1: wrap and delayed-update GEMMs as split BF16 tensor-core products
+  int tv;                  // 1: spinless t-V model (one species, bond fields)
+  int nfld;                // fields per slice: N, or 3N/2 bonds (tv)
   double U;
   double delta[2][2][2];   // [0 Hubbard, 1 Gutzwiller][spin][s=+1 -> 0, s=-1 -> 1]: e^{-2 sigma kappa s} - 1
   double vexp[2][2][2];    // same indexing: e^{sigma kappa s}
-  int8_t* fields;          // (Ltau+2) x N
+  double vtv[2][7];        // tv: [0 Hubbard-type slice, 1 Gutzwiller][m + 3]: e^{kappa m}, m = sum of the
+                           // site's three bond fields with sign +1 at A ends, -1 at B ends
+  int8_t* fields;          // (Ltau+2) x nfld
   void* G;                 // 2 x N x ld (T)
   const void* expKm;       // N x ld (T): e^{-dtau K}
   const void* expKp;       // N x ld (T): e^{+dtau K}
   const double* expKm64;   // N x N FP64
   const double* K64;       // N x N FP64
   const double* eps;       // N: staggered sublattice sign (+1 A, -1 B)
+  const int* bond_ends;    // tv: 3N/2 x 2 (A end, B end) of each bond
+  const int* site_bonds;   // tv: N x 3 bonds of each site
   const double* P;         // 2 x (N x nmax) FP64, column-major per spin (ld N)
   double* Rst;             // (nb+1) x 2 x (N x nmax) FP64
   double* Lst;             // (nb+1) x 2 x (N x nmax) FP64
@@ -106,7 +112,7 @@ PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 // Per-block buffers of the flip phase (kBlock x kBlock blocks of both spins,
 // uniforms, accepted sites); the layout is FlipBuf<T> in sweep.cu.
 PQMC_HDI constexpr size_t flipbuf_bytes(int tsize) {
-  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 4 * (size_t)kBlock * tsize + (size_t)kBlock * 4);
+  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 4 * (size_t)kBlock * tsize + 2 * (size_t)kBlock * 4);
 }
 
 PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {

@@ -96,6 +96,10 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
     return PQMC_EINVAL;
   }
   const pqmc_lattice& lt = spec->lattice;
+  if (lt.kind == PQMC_HONEYCOMB_TV) {
+    set_init_error("pqmc_green_noalloc: Hubbard lattices only");
+    return PQMC_EINVAL;
+  }
   const int N = lt.kind == PQMC_HONEYCOMB ? 2 * lt.Lx * lt.Ly : lt.Lx * lt.Ly;
   const int ld = (N + 3) & ~3;
   const int nup = spec->trial.N_up < 0 ? N / 2 : spec->trial.N_up;
@@ -174,6 +178,7 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
   ChainDesc d;
   memset(&d, 0, sizeof d);
   d.N = N; d.ld = ld; d.nup = nup; d.ndn = ndn; d.nmax = nmax;
+  d.nfld = N;
   d.Ltau = Ltau; d.nb = nb; d.n_stab = n_stab; d.kb = kBlock;
   d.U = spec->U;
   const double kap[2] = {hs_coupling(spec->dtau * spec->U), hs_coupling(spec->trial.g)};

@@ -312,6 +312,7 @@ struct FlipBuf {
   T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
   T rs[2][kBlock];                  // ratio R_sigma of each proposal of the block
   int sites[kBlock];                // block index of each accepted flip
+  int gsite[kBlock];                // its site
 };
 static_assert(sizeof(FlipBuf<double>) <= flipbuf_bytes(8) && sizeof(FlipBuf<float>) <= flipbuf_bytes(4),
               "flip buffer layout");
@@ -323,6 +324,8 @@ struct Smem {
   double vtab[2][2][2];             // e^{sigma kappa s}: [Gutzwiller?][spin][s = -1?]
   T vt[2][2][2];                    // the same in the path precision
   T vti[2][2][2];                   // and its inverse
+  T vtvT[2][7];                     // t-V: e^{kappa m}, m = -3..3, in the path precision
+  T vtvI[2][7];                     // and its inverse
   long long cyc[kPhases];           // per-phase clock cycles (thread 0)
   long long t_mark;
   signed char fr[kMaxN];            // fields of the staged slice
@@ -330,6 +333,7 @@ struct Smem {
   int piv;
   int nswap[2];
   int chol_bad;
+  int fperm[kBlock];                // row interchanges of the flush inverse (t-V)
   int staged;                       // slice held in fr, or -1
   double sign_running;
   double sign_spin[2];
@@ -378,20 +382,38 @@ struct Cta {
   __device__ const T* Ep() const { return reinterpret_cast<const T*>(c.expKp); }
   __device__ int nsig(int s) const { return s == 0 ? c.nup : c.ndn; }
   __device__ bool gutz(int tau) const { return tau == 0 || tau == c.Ltau + 1; }
-  // stage the fields of slice tau into shared memory (collective)
+  // fermion species carried by the chain: both spins, or one (t-V)
+  __device__ int nspec() const { return c.tv ? 1 : 2; }
+  // stage slice tau into shared memory (collective): the site fields, or for
+  // t-V the sum m_i of the site's three bond fields (+ at A ends, - at B ends)
   __device__ void stage(int tau) {
     __syncthreads();
-    const int8_t* f = c.fields + (long)tau * c.N;
-    for (int i = threadIdx.x; i < c.N; i += blockDim.x) sh.fr[i] = f[i];
+    const int8_t* f = c.fields + (long)tau * c.nfld;
+    if (c.tv) {
+      for (int i = threadIdx.x; i < c.N; i += blockDim.x) {
+        const int* sb = c.site_bonds + 3 * i;
+        const int m = (int)f[sb[0]] + (int)f[sb[1]] + (int)f[sb[2]];
+        sh.fr[i] = (signed char)((i & 1) ? -m : m);
+      }
+    } else {
+      for (int i = threadIdx.x; i < c.N; i += blockDim.x) sh.fr[i] = f[i];
+    }
     if (threadIdx.x == 0) sh.staged = tau;
     __syncthreads();
   }
   // diagonal of e^{V_sigma(s_tau)} at site i for the staged slice tau
   __device__ double vexp(int tau, int s, int i) const {
+    if (c.tv) return c.vtv[gutz(tau) ? 1 : 0][sh.fr[i] + 3];
     return sh.vtab[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
   }
-  __device__ T vexpT(int tau, int s, int i) const { return sh.vt[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1]; }
-  __device__ T vinvT(int tau, int s, int i) const { return sh.vti[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1]; }
+  __device__ T vexpT(int tau, int s, int i) const {
+    if (c.tv) return sh.vtvT[gutz(tau) ? 1 : 0][sh.fr[i] + 3];
+    return sh.vt[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
+  }
+  __device__ T vinvT(int tau, int s, int i) const {
+    if (c.tv) return sh.vtvI[gutz(tau) ? 1 : 0][sh.fr[i] + 3];
+    return sh.vti[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
+  }
   // charge the cycles since the last mark to phase ph (thread 0 only)
   __device__ void mark(int ph) {
     if (threadIdx.x == 0) {
@@ -424,6 +446,99 @@ __device__ __forceinline__ T uniform_of(uint64_t m53) {
   else return (float)(uint32_t)(m53 >> 29) * 0x1.0p-24f;
 }
 
+// Applies the a accepted flips of a block, recorded in fb (global sites
+// gsite, Delta per species cl), to the whole G of every species:
+//     G <- G - (E_S - G_{:,S}) Gamma (1 + (1 - G_SS) Gamma)^{-1} G_{S,:}
+// with G the G of the block start.  X = 1 + (1 - G_SS) Gamma is inverted in
+// place by one warp per species; Hubbard blocks need no pivoting (its pivots
+// are the accepted ratios), the bond blocks of the t-V model pivot on rows
+// (a single end of an accepted bond may have a vanishing ratio).
+template <typename T>
+__device__ void flush_block(Cta<T>& x, int a, bool pivot) {
+  const ChainDesc& c = x.c;
+  FlipBuf<T>& fb = *x.fb;
+  const int N = c.N, ld = c.ld, ns = x.nspec();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* Ubuf = x.Ub();                                    // kBlock x N  (U column-major, ld N)
+  T* Wbuf = x.Wb();                                    // kBlock x ld (rows G_{S,:})
+  PQMC_FOR_2D(sl, 0, ns * a, m, 0, a) {
+    const int s = sl >= a ? 1 : 0, l = sl - s * a;
+    const T g = x.G(s)[(long)fb.gsite[l] * ld + fb.gsite[m]];
+    fb.Tu[s][l][m] = ((l == m) ? T(1) : T(0)) + ((l == m ? T(1) : T(0)) - g) * fb.cl[s][m];
+  }
+  __syncthreads();
+  if (warp < ns) {
+    const int s = warp;
+    T (*X)[kBlock + 1] = fb.Tu[s];
+    int* perm = x.sh.fperm;
+    for (int p = 0; p < a; ++p) {
+      if (pivot) {
+        // largest |X_rp|, r >= p, ties to the lower row; swap rows r and p
+        T best = T(-1);
+        int bi = p;
+        if (lane >= p && lane < a) { best = fabs(X[lane][p]); bi = lane; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) perm[p] = bi;
+        if (bi != p && lane < a) {
+          const T t = X[p][lane];
+          X[p][lane] = X[bi][lane];
+          X[bi][lane] = t;
+        }
+        __syncwarp();
+      }
+      const T ip = T(1) / X[p][p];
+      const T xpl = lane < a ? X[p][lane] : T(0);
+      if (lane < a && lane != p)
+        for (int r = 0; r < a; ++r)
+          if (r != p) X[r][lane] = fma(-X[r][p] * ip, xpl, X[r][lane]);
+      __syncwarp();
+      if (lane < a) {
+        if (lane != p) X[p][lane] = xpl * ip;
+        X[lane][p] = lane == p ? ip : -X[lane][p] * ip;
+      }
+      __syncwarp();
+    }
+    if (pivot) {
+      // the row interchanges of the factorisation become column
+      // interchanges of the inverse, undone last step first
+      for (int p = a - 1; p >= 0; --p) {
+        const int q = perm[p];
+        if (q != p && lane < a) {
+          const T t = X[lane][p];
+          X[lane][p] = X[lane][q];
+          X[lane][q] = t;
+        }
+        __syncwarp();
+      }
+    }
+    for (int l = 0; l < a; ++l)
+      if (lane < a) X[l][lane] *= fb.cl[s][l];
+  }
+  __syncthreads();
+  // per species: A_S = E_S - G_{:,S} (N x a, column-major) and W = G_{S,:}
+  // (a x N) gathered before G changes, then MW = M W and G -= A_S MW
+  T* MW = reinterpret_cast<T*>(x.scr + x.L.mw);
+  for (int s = 0; s < ns; ++s) {
+    T* Gs = x.G(s);
+    PQMC_FOR_2D(m, 0, a, i, 0, N) {
+      const int col = fb.gsite[m];
+      Ubuf[(long)m * N + i] = (i == col ? T(1) : T(0)) - Gs[(long)i * ld + col];
+    }
+    PQMC_FOR_2D(l, 0, a, q, 0, N) Wbuf[(long)l * ld + q] = Gs[(long)fb.gsite[l] * ld + q];
+    __syncthreads();
+    cta_gemm<T>(a, N, a, &fb.Tu[s][0][0], kBlock + 1, 1, Wbuf, ld, 1, MW, ld, 1, EpiStore());
+    __syncthreads();
+    path_gemm<T>(c, N, N, a, Ubuf, 1, N, MW, ld, 1, Gs, ld, 1, EpiSub());
+    __syncthreads();
+  }
+  x.mark(kPhFlush);
+}
+
 template <typename T>
 __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const ChainDesc& c = x.c;
@@ -432,9 +547,7 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const int N = c.N, ld = c.ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int kap = x.gutz(tau) ? 1 : 0;
-  int8_t* f = c.fields + (long)tau * N;
-  T* Ubuf = x.Ub();                                    // kBlock x N  (U column-major, ld N)
-  T* Wbuf = x.Wb();                                    // kBlock x ld (rows G_{S,:})
+  int8_t* f = c.fields + (long)tau * c.nfld;
   const T dl[2][2] = {{(T)c.delta[kap][0][0], (T)c.delta[kap][0][1]}, {(T)c.delta[kap][1][0], (T)c.delta[kap][1][1]}};
 
   for (int i0 = 0; i0 < N; i0 += kBlock) {
@@ -484,6 +597,7 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
             }
             if (s == 0 && lane == 0) {
               fb.sites[a] = j;
+              fb.gsite[a] = i0 + j;
               fb.cl[0][a] = ds;
               fb.cl[1][a] = dl[1][si];
               nneg += R < T(0) ? 1 : 0;
@@ -506,51 +620,122 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
     const int a = sh.na;
     if (a == 0) continue;
 
-    // X = 1 + (1 - G_SS) Gamma (block-start G), inverted in place by one warp
-    // per spin; then M = Gamma X^{-1} (stored in Tu)
-    PQMC_FOR_2D(sl, 0, 2 * a, m, 0, a) {
-      const int s = sl >= a ? 1 : 0, l = sl - s * a;
-      const T g = x.G(s)[(long)(i0 + fb.sites[l]) * ld + i0 + fb.sites[m]];
-      fb.Tu[s][l][m] = ((l == m) ? T(1) : T(0)) + ((l == m ? T(1) : T(0)) - g) * fb.cl[s][m];
-    }
-    __syncthreads();
-    if (warp < 2) {
-      const int s = warp;
-      T (*X)[kBlock + 1] = fb.Tu[s];
-      for (int p = 0; p < a; ++p) {
-        const T ip = T(1) / X[p][p];
-        const T xpl = lane < a ? X[p][lane] : T(0);
-        if (lane < a && lane != p)
-          for (int r = 0; r < a; ++r)
-            if (r != p) X[r][lane] = fma(-X[r][p] * ip, xpl, X[r][lane]);
-        __syncwarp();
-        if (lane < a) {
-          if (lane != p) X[p][lane] = xpl * ip;
-          X[lane][p] = lane == p ? ip : -X[lane][p] * ip;
+    flush_block(x, a, false);
+  }
+}
+
+// Metropolis updates of one slice of the spinless t-V model: the bonds in
+// blocks of 16 of one class (a class is a perfect matching, so a block
+// touches 32 distinct sites W).  Warp 0 holds G_WW in registers, lane q the
+// column of site W[q] (pair p = bond p of the block: A end in lane 2p, B end
+// in lane 2p+1); lane p draws the uniform of bond p.  Bond p's flip changes
+// V at its two ends by Gamma = diag(Delta_A, Delta_B) and is accepted with
+// R = det(1 + Gamma (1 - G_SS)); an accepted flip updates the rows and
+// columns of the later pairs by the rank-2 form
+//     G_rq <- G_rq + sum_{s in S} G_rs (M G_{S,q})_s,  M = Gamma (1 + (1 - G_SS) Gamma)^{-1}.
+// The accepted ends then go to flush_block as one set.
+template <typename T>
+__device__ void update_slice_tv(Cta<T>& x, int tau, uint32_t sweep) {
+  const ChainDesc& c = x.c;
+  Smem<T>& sh = x.sh;
+  FlipBuf<T>& fb = *x.fb;
+  const int ld = c.ld, nc = c.N / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kap = x.gutz(tau) ? 1 : 0;
+  int8_t* f = c.fields + (long)tau * c.nfld;
+  // Delta at the A end (coupled like spin up) and at the B end, field +1 / -1
+  const T dA[2] = {(T)c.delta[kap][0][0], (T)c.delta[kap][0][1]};
+  const T dB[2] = {(T)c.delta[kap][1][0], (T)c.delta[kap][1][1]};
+  constexpr int kPairs = kBlock / 2;
+  for (int k = 0; k < 3; ++k) {
+    for (int c0 = 0; c0 < nc; c0 += kPairs) {
+      const int np = min(kPairs, nc - c0);
+      if (warp == 0) {
+        const bool on = (lane >> 1) < np;
+        const int wq = on ? c.bond_ends[2 * (3 * (c0 + (lane >> 1)) + k) + (lane & 1)] : 0;
+        T g[kBlock];
+        const T* G0 = x.G(0);
+#pragma unroll
+        for (int r = 0; r < kBlock; ++r) {
+          const int wr = __shfl_sync(0xffffffffu, wq, r);
+          g[r] = (on && (r >> 1) < np) ? G0[(long)wr * ld + wq] : T(0);
         }
-        __syncwarp();
+        T up = T(2);
+        int fp = 1;
+        if (lane < np) {
+          const int b = 3 * (c0 + lane) + k;
+          const U4 w = philox4x32_10((uint32_t)b, (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
+                                     (uint32_t)(x.seed >> 32));
+          up = uniform_of<T>(((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11));
+          fp = (int)f[b];
+        }
+        int a = 0, bad = 0, nneg = 0;
+        const long long pos0 = sh.acc_pos;
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          if (p < np) {
+            const int si = __shfl_sync(0xffffffffu, fp, p) > 0 ? 0 : 1;
+            const T di = dA[si], dj = dB[si];
+            const T gii = __shfl_sync(0xffffffffu, g[2 * p], 2 * p);
+            const T gjj = __shfl_sync(0xffffffffu, g[2 * p + 1], 2 * p + 1);
+            const T gij = __shfl_sync(0xffffffffu, g[2 * p], 2 * p + 1);
+            const T gji = __shfl_sync(0xffffffffu, g[2 * p + 1], 2 * p);
+            // R = det(1 + Gamma (1 - G_SS))
+            const T m00 = T(1) + di * (T(1) - gii), m01 = -di * gij;
+            const T m10 = -dj * gji, m11 = T(1) + dj * (T(1) - gjj);
+            const T R = m00 * m11 - m01 * m10;
+            const bool acc = __shfl_sync(0xffffffffu, (int)(up < (R < T(0) ? -R : R)), p) != 0;
+            if (lane == 0) {
+              if (!isfinite(R)) bad = 1;
+              if (pos0 + p < c.acc_cap) c.acc_log[pos0 + p] = acc ? 1 : 0;
+            }
+            if (acc) {
+              // X = 1 + (1 - G_SS) Gamma, M = Gamma X^{-1}
+              const T x00 = T(1) + (T(1) - gii) * di, x01 = -gij * dj;
+              const T x10 = -gji * di, x11 = T(1) + (T(1) - gjj) * dj;
+              const T inv = T(1) / (x00 * x11 - x01 * x10);
+              const T M00 = di * (x11 * inv), M01 = di * (-x01 * inv);
+              const T M10 = dj * (-x10 * inv), M11 = dj * (x00 * inv);
+              const bool fut = lane >= 2 * p + 2;
+              const T y0 = fut ? M00 * g[2 * p] + M01 * g[2 * p + 1] : T(0);
+              const T y1 = fut ? M10 * g[2 * p] + M11 * g[2 * p + 1] : T(0);
+#pragma unroll
+              for (int r = 2 * p + 2; r < kBlock; ++r) {
+                const T gri = __shfl_sync(0xffffffffu, g[r], 2 * p);
+                const T grj = __shfl_sync(0xffffffffu, g[r], 2 * p + 1);
+                g[r] = fma(gri, y0, fma(grj, y1, g[r]));
+              }
+              if (lane == p) {
+                fp = -fp;
+                f[3 * (c0 + p) + k] = (int8_t)fp;
+              }
+              const int wi = __shfl_sync(0xffffffffu, wq, 2 * p), wj = __shfl_sync(0xffffffffu, wq, 2 * p + 1);
+              if (lane == 0) {
+                fb.gsite[a] = wi;
+                fb.cl[0][a] = di;
+                fb.gsite[a + 1] = wj;
+                fb.cl[0][a + 1] = dj;
+                nneg += R < T(0) ? 1 : 0;
+              }
+              a += 2;
+            }
+          }
+        }
+        if (lane == 0) {
+          sh.na = a;
+          sh.acc_pos = pos0 + np;
+          sh.n_prop += np;
+          sh.n_acc += a / 2;
+          if (nneg & 1) sh.sign_running = -sh.sign_running;
+          if (bad) sh.err |= kErrNaN;
+        }
       }
-      for (int l = 0; l < a; ++l)
-        if (lane < a) X[l][lane] *= fb.cl[s][l];
+      __syncthreads();
+      x.mark(kPhFlip);
+      const int a = sh.na;
+      if (a == 0) continue;
+      flush_block(x, a, true);
     }
-    __syncthreads();
-    // per spin: A_S = E_S - G_{:,S} (N x a, column-major) and W = G_{S,:}
-    // (a x N) gathered before G changes, then MW = M W and G -= A_S MW
-    T* MW = reinterpret_cast<T*>(x.scr + x.L.mw);
-    for (int s = 0; s < 2; ++s) {
-      T* Gs = x.G(s);
-      PQMC_FOR_2D(m, 0, a, i, 0, N) {
-        const int col = i0 + fb.sites[m];
-        Ubuf[(long)m * N + i] = (i == col ? T(1) : T(0)) - Gs[(long)i * ld + col];
-      }
-      PQMC_FOR_2D(l, 0, a, q, 0, N) Wbuf[(long)l * ld + q] = Gs[(long)(i0 + fb.sites[l]) * ld + q];
-      __syncthreads();
-      cta_gemm<T>(a, N, a, &fb.Tu[s][0][0], kBlock + 1, 1, Wbuf, ld, 1, MW, ld, 1, EpiStore());
-      __syncthreads();
-      path_gemm<T>(c, N, N, a, Ubuf, 1, N, MW, ld, 1, Gs, ld, 1, EpiSub());
-      __syncthreads();
-    }
-    x.mark(kPhFlush);
   }
 }
 
@@ -566,14 +751,14 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
   T* Gt = x.Gt();
   x.stage(tau);
   if (dir > 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < x.nspec(); ++s) {
       T* Gs = x.G(s);
       PQMC_FOR_2D(i, 0, N, j, 0, N) Gs[(long)i * ld + j] *= x.vexpT(tau, s, i) * x.vinvT(tau, s, j);
     }
     __syncthreads();
     if (gz) return;
     // Gt = e^{-dtau K} G, G = Gt e^{+dtau K}
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < x.nspec(); ++s) {
       path_gemm<T>(c, N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
       __syncthreads();
       path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
@@ -581,14 +766,14 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
     }
   } else {
     if (!gz) {
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < x.nspec(); ++s) {
         path_gemm<T>(c, N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
         __syncthreads();
         path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
         __syncthreads();
       }
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < x.nspec(); ++s) {
       T* Gs = x.G(s);
       PQMC_FOR_2D(i, 0, N, j, 0, N) Gs[(long)i * ld + j] *= x.vexpT(tau, s, j) * x.vinvT(tau, s, i);
     }
@@ -986,7 +1171,7 @@ __device__ void push_R(Cta<T>& x, int b) {
   const ChainDesc& c = x.c;
   const int N = c.N, n_stab = c.n_stab;
   double* M = x.M64();
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < x.nspec(); ++s) {
     const int n = x.nsig(s);
     const double* P = c.P + (long)s * N * c.nmax;
     T* Mt = x.Mt();
@@ -1033,7 +1218,7 @@ __device__ void push_L(Cta<T>& x, int b) {
   const ChainDesc& c = x.c;
   const int N = c.N, n_stab = c.n_stab;
   double* M = x.M64();
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < x.nspec(); ++s) {
     const int n = x.nsig(s);
     const double* P = c.P + (long)s * N * c.nmax;
     T* Mt = x.Mt();
@@ -1109,7 +1294,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
   double la[2], sg[2];
   gj_invert2(x, n, O, la, sg);
   x.mark(kPhLU);
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < x.nspec(); ++s) {
     // Y = X Q_L^T (n x N), G_fresh = 1 - Q_R Y, in the path precision
     const T* qr = reinterpret_cast<const T*>(QR[s]);
     const T* ql = reinterpret_cast<const T*>(QL[s]);
@@ -1145,6 +1330,11 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     sign_total *= s_tot;
     __syncthreads();
   }
+  if (threadIdx.x == 0)
+    for (int s = x.nspec(); s < 2; ++s) {
+      sh.logw_spin[s] = 0.0;
+      sh.sign_spin[s] = 1.0;
+    }
   x.mark(kPhAssemble);
   const double dm = cta_max((double)dmax, sh.red);
   if (threadIdx.x == 0) {
@@ -1165,9 +1355,53 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
 // staggered S^z structure factor S = (1/N^2) sum_ij eps_i eps_j <S^z_i S^z_j>
 // = [(sum_i eps_i m_i)^2 + sum_s sum_ij eps_i eps_j (delta_ij - G_s,ji) G_s,ij]
 // / (4 N^2), m_i = n_i,up - n_i,dn (the spins are independent at fixed fields).
+// Wick estimates of the spinless t-V model on the fresh G at the middle
+// slice: E/site of Eq. (4), interaction energy/site
+// V sum_<ij> [(n_i - 1/2)(n_j - 1/2) - G_ji G_ij] / N, kinetic/site, the weight
+// sign, the running sign, and S_CDW = [(sum_i eps_i (n_i - 1/2))^2 +
+// sum_ij eps_i eps_j (delta_ij - G_ji) G_ij] / N^2.
+template <typename T>
+__device__ void measure_tv(Cta<T>& x) {
+  const ChainDesc& c = x.c;
+  Smem<T>& sh = x.sh;
+  const int N = c.N, ld = c.ld;
+  const T* G = x.G(0);
+  double ek = 0.0, eb = 0.0, st = 0.0, ex = 0.0;
+  PQMC_FOR_2D(i, 0, N, j, 0, N) {
+    const double gji = (i == j ? 1.0 : 0.0) - (double)G[(long)j * ld + i];
+    ek += c.K64[(long)i * N + j] * gji;
+    ex += c.eps[i] * c.eps[j] * gji * (double)G[(long)i * ld + j];
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) st += c.eps[i] * (0.5 - (double)G[(long)i * ld + i]);
+  for (int b = threadIdx.x; b < c.nfld; b += blockDim.x) {
+    const int i = c.bond_ends[2 * b], j = c.bond_ends[2 * b + 1];
+    const double di = 0.5 - (double)G[(long)i * ld + i], dj = 0.5 - (double)G[(long)j * ld + j];
+    eb += di * dj - (double)G[(long)j * ld + i] * (double)G[(long)i * ld + j];
+  }
+  ek = cta_sum(ek, sh.red);
+  eb = cta_sum(eb, sh.red) * c.U;
+  st = cta_sum(st, sh.red);
+  ex = cta_sum(ex, sh.red);
+  if (threadIdx.x == 0) {
+    const int m = c.st->n_meas;
+    const double rec[kRecord] = {sh.sign_spin[0] * sh.sign_spin[1], (ek + eb) / N, eb / N, ek / N,
+                                 sh.sign_running, (st * st + ex) / ((double)N * N)};
+    for (int k = 0; k < kRecord; ++k) {
+      if (m < c.max_meas) c.meas[(long)m * kRecord + k] = rec[k];
+      c.last[k] = rec[k];
+    }
+    c.st->n_meas = m + 1;
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ void measure(Cta<T>& x) {
   const ChainDesc& c = x.c;
+  if (c.tv) {
+    measure_tv(x);
+    return;
+  }
   Smem<T>& sh = x.sh;
   const int N = c.N, ld = c.ld;
   double ek = 0.0, dc = 0.0, st = 0.0, ex = 0.0;
@@ -1209,7 +1443,8 @@ template <typename T>
 __device__ void sweep_up(Cta<T>& x, uint32_t sweep, bool do_measure) {
   const ChainDesc& c = x.c;
   for (int tau = 0; tau <= c.Ltau + 1; ++tau) {
-    update_slice(x, tau, sweep);
+    if (c.tv) update_slice_tv(x, tau, sweep);
+    else update_slice(x, tau, sweep);
     wrap(x, tau, +1);
     x.mark(kPhWrap);
     if (tau <= c.Ltau && tau % c.n_stab == 0) {
@@ -1229,7 +1464,8 @@ __device__ void sweep_down(Cta<T>& x, uint32_t sweep, bool do_measure) {
   for (int tau = c.Ltau + 1; tau >= 0; --tau) {
     wrap(x, tau, -1);
     x.mark(kPhWrap);
-    update_slice(x, tau, sweep);
+    if (c.tv) update_slice_tv(x, tau, sweep);
+    else update_slice(x, tau, sweep);
     const int t1 = tau - 1;
     if (t1 >= 0 && t1 % c.n_stab == 0) {
       const int b = t1 / c.n_stab;
@@ -1263,6 +1499,11 @@ __device__ void load_state(Cta<T>& x) {
     x.sh.vtab[k][s][si] = x.c.vexp[k][s][si];
     x.sh.vt[k][s][si] = (T)x.c.vexp[k][s][si];
     x.sh.vti[k][s][si] = (T)(1.0 / x.c.vexp[k][s][si]);
+  }
+  if (threadIdx.x < 14) {
+    const int k = threadIdx.x / 7, m = threadIdx.x - 7 * k;
+    x.sh.vtvT[k][m] = (T)x.c.vtv[k][m];
+    x.sh.vtvI[k][m] = (T)(1.0 / x.c.vtv[k][m]);
   }
   if (threadIdx.x < kPhases) x.sh.cyc[threadIdx.x] = 0;
   if (threadIdx.x == 0) x.sh.t_mark = clock64();

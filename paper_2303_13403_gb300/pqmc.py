@@ -16,7 +16,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTAB, ENAN, ETIMEOUT = range(7)
 STATUS = {0: "PQMC_OK", 1: "PQMC_EINVAL", 2: "PQMC_ENOMEM", 3: "PQMC_ECUDA", 4: "PQMC_ESTAB",
           5: "PQMC_ENAN", 6: "PQMC_ETIMEOUT"}
 FP64, FP32, BF16X3 = 0, 1, 2
-HONEYCOMB, SQUARE = 0, 1
+HONEYCOMB, SQUARE, HONEYCOMB_TV = 0, 1, 2
 
 
 class Lattice(C.Structure):
@@ -175,9 +175,9 @@ class Context:
         return o.as_dict()
 
     def dims(self, chain=0):
-        d = (C.c_int * 6)()
+        d = (C.c_int * 7)()
         _check(load().pqmc_get_dims(self._h, chain, d), self._h)
-        return dict(zip(("N", "N_up", "N_dn", "Ltau", "n_stab", "delay_k"), list(d)))
+        return dict(zip(("N", "N_up", "N_dn", "Ltau", "n_stab", "delay_k", "n_fields"), list(d)))
 
     def measurements(self, chain=0, cap=1 << 16):
         out = np.zeros((cap, RECORD))
@@ -208,7 +208,7 @@ class Context:
 
     def fields(self, chain=0):
         d = self.dims(chain)
-        out = np.zeros((d["Ltau"] + 2, d["N"]), dtype=np.int8)
+        out = np.zeros((d["Ltau"] + 2, d["n_fields"]), dtype=np.int8)
         _check(load().pqmc_get_fields(self._h, chain, out.ctypes.data_as(C.POINTER(C.c_int8))), self._h)
         return out
 

@@ -11,7 +11,9 @@ quadratic fit over the points around it (host-side analysis of the measured
 energies; every Monte Carlo step runs in the CUDA kernels).
 
 Run ``python -m paper_2303_13403_gb300.variational --L 6`` for the 11 x 11
-scan of Fig. 1 (g in [0, 1], M_N in [0, 0.3]) at U = 3.5 and 4.0.
+scan of Fig. 1 (g in [0, 1], M_N in [0, 0.3]) at U = 3.5 and 4.0, and with
+``--tv --U 1.35 1.6`` the same scan of the spinless t-V trial of Eq. (5)
+(bond g, CDW field Delta_C), whose optimum the paper uses without quoting it.
 """
 import argparse
 import json
@@ -26,7 +28,12 @@ M_VALUES = tuple(np.round(0.03 * np.arange(11), 10))
 
 
 def grid_specs(U, L, g_values=G_VALUES, m_values=M_VALUES, dtau=0.1, kind=workloads.HONEYCOMB):
-    """ChainSpecs of one Theta = 0 grid, row-major over (g, M_N)."""
+    """ChainSpecs of one Theta = 0 grid, row-major over (g, M_N).  For the
+    spinless t-V model (kind HONEYCOMB_TV) U is V and M_N the CDW field
+    Delta_C of the trial of Eq. (5)."""
+    if kind == workloads.HONEYCOMB_TV:
+        return [workloads.tv_honeycomb(L, V=U, g=float(g), Delta_C=float(m), two_theta=0.0, dtau=dtau)
+                for g in g_values for m in m_values]
     return [workloads.ChainSpec(kind=kind, Lx=L, Ly=L, U=U, dtau=dtau, two_theta=0.0, g=float(g),
                                 M_N=float(m))
             for g in g_values for m in m_values]
@@ -116,11 +123,13 @@ def main():
     ap.add_argument("--warm", type=int, default=50)
     ap.add_argument("--meas", type=int, default=400)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--tv", action="store_true", help="spinless t-V model (--U are V values)")
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     prec = {v: k for k, v in workloads.PRECISION_NAMES.items()}[a.prec]
-    r = scan(a.U, a.L, a.chains, a.warm, a.meas, prec)
+    kind = workloads.HONEYCOMB_TV if a.tv else workloads.HONEYCOMB
+    r = scan(a.U, a.L, a.chains, a.warm, a.meas, prec, kind=kind)
     line = {"L": a.L, "chains": r["chains"], "sweeps": r["sweeps"], "seconds": round(r["seconds"], 3)}
     for U in a.U:
         x = r[U]

@@ -14,6 +14,7 @@ import numpy as np
 
 HONEYCOMB = 0
 SQUARE = 1
+HONEYCOMB_TV = 2        # spinless t-V model on the honeycomb lattice (U holds V, M_N holds Delta_C)
 
 FP64 = 0
 FP32 = 1
@@ -39,7 +40,12 @@ class ChainSpec:
 
     @property
     def n_sites(self):
-        return 2 * self.Lx * self.Ly if self.kind == HONEYCOMB else self.Lx * self.Ly
+        return self.Lx * self.Ly if self.kind == SQUARE else 2 * self.Lx * self.Ly
+
+    @property
+    def n_fields(self):
+        """Ising fields per slice: one per site, or one per bond (t-V)."""
+        return 3 * self.Lx * self.Ly if self.kind == HONEYCOMB_TV else self.n_sites
 
     @property
     def n_slices(self):
@@ -52,6 +58,12 @@ class ChainSpec:
 
 def honeycomb(L, **kw):
     return ChainSpec(kind=HONEYCOMB, Lx=L, Ly=L, **kw)
+
+
+def tv_honeycomb(L, V=1.6, g=0.0, Delta_C=0.0, two_theta=4.0, dtau=0.1, Ly=None, **kw):
+    """Spinless t-V chain on the L x L honeycomb lattice at half filling."""
+    return ChainSpec(kind=HONEYCOMB_TV, Lx=L, Ly=L if Ly is None else Ly, U=V, dtau=dtau, two_theta=two_theta,
+                     g=g, M_N=Delta_C, n_up=-1, n_dn=0, **kw)
 
 
 # Plain PQMC with a Slater trial on the 18-site honeycomb cluster: 100 slices,
@@ -89,4 +101,4 @@ def random_fields(spec, seed):
     """Seeded uniform +-1 fields, shape (Ltau + 2, N), int8."""
     rng = np.random.default_rng(seed)
     return rng.choice(np.array([-1, 1], dtype=np.int8),
-                      size=(spec.n_slices + 2, spec.n_sites))
+                      size=(spec.n_slices + 2, spec.n_fields))
