@@ -51,6 +51,13 @@ def test_invalid_specs_rejected_before_device(lib):
         workloads.ChainSpec(Lx=0, Ly=3),
         workloads.ChainSpec(Lx=3, Ly=3, dtau=-0.1),
         workloads.ChainSpec(Lx=3, Ly=3, g=-0.5),
+        workloads.ChainSpec(Lx=3, Ly=3, U=-1.0),
+        workloads.ChainSpec(Lx=3, Ly=3, two_theta=-0.2),
+        workloads.ChainSpec(kind=7, Lx=3, Ly=3),                # unknown lattice kind
+        workloads.honeycomb(23, two_theta=0.0),                 # 1058 sites: above the 1024-site maximum
+        workloads.ChainSpec(kind=workloads.SQUARE, Lx=32, Ly=32, two_theta=0.0,
+                            n_up=600, n_dn=600),                # N_sigma above 512
+        workloads.ChainSpec(kind=workloads.HONEYCOMB_TV, Lx=3, Ly=3, n_dn=3),   # t-V has one species
     ]
     for s in bad:
         with pytest.raises(pqmc.PQMCError) as e:
@@ -116,3 +123,9 @@ def test_variational_quadratic_minimum():
     specs = variational.grid_specs(3.5, 6)
     assert len(specs) == 121 and all(sp.two_theta == 0.0 and sp.n_sites == 72 for sp in specs)
     assert specs[12].g == 0.1 and specs[12].M_N == 0.03
+
+
+def test_empty_batch_rejected(lib):
+    with pytest.raises(pqmc.PQMCError) as e:
+        pqmc.Context([])
+    assert e.value.status == pqmc.EINVAL
