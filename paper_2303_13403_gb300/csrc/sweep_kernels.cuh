@@ -321,11 +321,12 @@ template <typename T>
 struct Smem {
   ChainDesc desc;                   // this chain's descriptor, copied in at launch
   double red[32];                   // reduction scratch
-  double vtab[2][2][2];             // e^{sigma kappa s}: [Gutzwiller?][spin][s = -1?]
-  T vt[2][2][2];                    // the same in the path precision
-  T vti[2][2][2];                   // and its inverse
-  T vtvT[2][7];                     // t-V: e^{kappa m}, m = -3..3, in the path precision
-  T vtvI[2][7];                     // and its inverse
+  // e^{V_sigma} of one site as a function of m = the staged value fr[i]
+  // (a site field +-1, or for t-V the signed sum of the site's bond fields,
+  // -3..3): [Gutzwiller?][spin][m + 3]; unused entries are 1
+  double vtab[2][2][7];
+  T vt[2][2][7];                    // the same in the path precision
+  T vti[2][2][7];                   // and its inverse
   long long cyc[kPhases];           // per-phase clock cycles (thread 0)
   long long t_mark;
   signed char fr[kMaxN];            // fields of the staged slice
@@ -402,18 +403,9 @@ struct Cta {
     __syncthreads();
   }
   // diagonal of e^{V_sigma(s_tau)} at site i for the staged slice tau
-  __device__ double vexp(int tau, int s, int i) const {
-    if (c.tv) return c.vtv[gutz(tau) ? 1 : 0][sh.fr[i] + 3];
-    return sh.vtab[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
-  }
-  __device__ T vexpT(int tau, int s, int i) const {
-    if (c.tv) return sh.vtvT[gutz(tau) ? 1 : 0][sh.fr[i] + 3];
-    return sh.vt[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
-  }
-  __device__ T vinvT(int tau, int s, int i) const {
-    if (c.tv) return sh.vtvI[gutz(tau) ? 1 : 0][sh.fr[i] + 3];
-    return sh.vti[gutz(tau) ? 1 : 0][s][sh.fr[i] > 0 ? 0 : 1];
-  }
+  __device__ double vexp(int tau, int s, int i) const { return sh.vtab[gutz(tau) ? 1 : 0][s][sh.fr[i] + 3]; }
+  __device__ T vexpT(int tau, int s, int i) const { return sh.vt[gutz(tau) ? 1 : 0][s][sh.fr[i] + 3]; }
+  __device__ T vinvT(int tau, int s, int i) const { return sh.vti[gutz(tau) ? 1 : 0][s][sh.fr[i] + 3]; }
   // charge the cycles since the last mark to phase ph (thread 0 only)
   __device__ void mark(int ph) {
     if (threadIdx.x == 0) {
@@ -1494,16 +1486,17 @@ __device__ void load_state(Cta<T>& x) {
     x.sh.logw_spin[0] = st.logw[0][0];
     x.sh.logw_spin[1] = st.logw[1][0];
   }
-  if (threadIdx.x < 8) {
-    const int k = threadIdx.x >> 2, s = (threadIdx.x >> 1) & 1, si = threadIdx.x & 1;
-    x.sh.vtab[k][s][si] = x.c.vexp[k][s][si];
-    x.sh.vt[k][s][si] = (T)x.c.vexp[k][s][si];
-    x.sh.vti[k][s][si] = (T)(1.0 / x.c.vexp[k][s][si]);
-  }
-  if (threadIdx.x < 14) {
-    const int k = threadIdx.x / 7, m = threadIdx.x - 7 * k;
-    x.sh.vtvT[k][m] = (T)x.c.vtv[k][m];
-    x.sh.vtvI[k][m] = (T)(1.0 / x.c.vtv[k][m]);
+  if (threadIdx.x < 28) {
+    const int k = threadIdx.x / 14, sp = (threadIdx.x / 7) % 2, m = threadIdx.x % 7 - 3;
+    double v = 1.0;
+    if (x.c.tv) {
+      if (sp == 0) v = x.c.vtv[k][m + 3];
+    } else if (m == 1 || m == -1) {
+      v = x.c.vexp[k][sp][m > 0 ? 0 : 1];
+    }
+    x.sh.vtab[k][sp][m + 3] = v;
+    x.sh.vt[k][sp][m + 3] = (T)v;
+    x.sh.vti[k][sp][m + 3] = (T)(1.0 / v);
   }
   if (threadIdx.x < kPhases) x.sh.cyc[threadIdx.x] = 0;
   if (threadIdx.x == 0) x.sh.t_mark = clock64();
