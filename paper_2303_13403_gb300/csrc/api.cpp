@@ -2,7 +2,8 @@
 //
 // Host side: validates the chain specs, builds the model in FP64 (model.cpp),
 // draws the initial fields with Philox, lays out one device arena per context
-// and drives the kernels of sweep.cu on the context's stream.
+// and drives the sweep kernels (sweep_kernels.cuh, dispatched by sweep.cu) on
+// the context's stream.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -1,5 +1,5 @@
-// Per-chain descriptors shared by the CUDA kernels (sweep.cu) and the host
-// side of the C-ABI (api.cpp). Plain data: device pointers and sizes.
+// Per-chain descriptors shared by the CUDA kernels (sweep_kernels.cuh) and the
+// host side of the C-ABI (api.cpp). Plain data: device pointers and sizes.
 #pragma once
 #include <stdint.h>
 
@@ -9,7 +9,6 @@ constexpr int kBlock = 32;        // sites per delayed-update block (one warp)
 constexpr int kMaxN = 1024;       // sites per chain
 constexpr int kMaxSigma = 512;    // particles per spin
 constexpr int kQRParts = 8;       // row chunks of the column dots in the Householder QR
-constexpr int kThreads = 256;     // threads per chain CTA
 constexpr int kRecord = 6;        // doubles per measurement record
 constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
 
@@ -17,6 +16,8 @@ constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
 enum : int {
   kPhFlip = 0, kPhFlush, kPhWrap, kPhStack, kPhQR, kPhRefresh, kPhMeasure, kPhTotal,
   kPhQRForm, kPhOverlap, kPhLU, kPhAssemble, kPhGJPivot, kPhGJElim, kPhGJTail, kPhases
+  // (kPhLU: the marker after the Gauss-Jordan inverse, which the three kPhGJ
+  // phases already cover; kept so that the counter layout stays fixed)
 };
 
 // error bits written by the kernels
@@ -110,7 +111,7 @@ struct ScratchLayout {
 PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 // Per-block buffers of the flip phase (kBlock x kBlock blocks of both spins,
-// uniforms, accepted sites); the layout is FlipBuf<T> in sweep.cu.
+// ratios, accepted sites); the layout is FlipBuf<T> in sweep_kernels.cuh.
 PQMC_HDI constexpr size_t flipbuf_bytes(int tsize) {
   return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 4 * (size_t)kBlock * tsize + 2 * (size_t)kBlock * 4);
 }
