@@ -133,9 +133,11 @@ typedef struct {
                                accept_log proposals per chain (test hook) */
     int max_meas;           /* capacity of per-sweep measurement records per chain (0 = 4096) */
     void* stream;           /* cudaStream_t to run on, or NULL for a library-owned stream */
-    int cta_threads;        /* threads of the CTA that runs one chain: 64, 128 or 256; 0 picks
-                               64 for FP64 and 256 otherwise. Smaller CTAs put more chains
-                               on one SM (FP64: 256/cta_threads per SM, others twice that) */
+    int cta_threads;        /* threads of the CTA that runs one chain: 64, 128, 256, or 512
+                               (reduced paths only, one chain per SM); 0 picks 64 for FP64,
+                               and for the reduced paths 256, or 512 when a chain has 128
+                               sites or more. Smaller CTAs put more chains on one SM
+                               (FP64: 256/cta_threads per SM, others twice that) */
     int dense_chains;       /* reduced paths only: kernels built for twice as many chains per SM
                                (fewer registers per thread); needs cta_threads 64 or 128 */
 } pqmc_opts;

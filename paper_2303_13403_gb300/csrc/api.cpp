@@ -196,8 +196,11 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (o.delay_k != kBlock) return fail(nullptr, PQMC_EINVAL, "delay_k must be 0 or 32");
   if (o.max_meas <= 0) o.max_meas = 4096;
   if (o.accept_log < 0) return fail(nullptr, PQMC_EINVAL, "accept_log < 0");
-  if (o.cta_threads != 0 && o.cta_threads != 64 && o.cta_threads != 128 && o.cta_threads != 256)
-    return fail(nullptr, PQMC_EINVAL, "cta_threads must be 0, 64, 128 or 256");
+  if (o.cta_threads != 0 && o.cta_threads != 64 && o.cta_threads != 128 && o.cta_threads != 256 &&
+      o.cta_threads != 512)
+    return fail(nullptr, PQMC_EINVAL, "cta_threads must be 0, 64, 128, 256 or 512");
+  if (o.cta_threads == 512 && (o.prec == PQMC_FP64 || o.dense_chains))
+    return fail(nullptr, PQMC_EINVAL, "cta_threads 512 is built for the reduced paths only");
   if (o.dense_chains && o.prec != PQMC_FP64 && o.cta_threads == 256)
     return fail(nullptr, PQMC_EINVAL, "dense_chains needs cta_threads 64 or 128");
   for (int c = 0; c < n; ++c) {
@@ -291,10 +294,15 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     h.off_state = take(sizeof(ChainState));
   }
   ctx->off_last = take((size_t)n * kRecord * 8);
-  // default CTA size (measured on GB300 at 72 sites): the FP64 path packs 4
-  // chains of 64 threads per SM; the reduced paths 2 chains of 256 threads,
-  // whose G and scratch then fit in shared memory
-  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : 256);
+  // default CTA size (measured on GB300): the FP64 path packs 4 chains of 64
+  // threads per SM; the reduced paths 2 chains of 256 threads, whose G and
+  // scratch then fit in shared memory at 72 sites, and one chain of 512
+  // threads per SM once a chain has 128 sites or more (its G lives in global
+  // memory and more warps hide the latency: 1.4-1.6x at 162-648 sites)
+  int nmax_sites = 0;
+  for (const HostChain& h : ctx->chains) nmax_sites = std::max(nmax_sites, h.N);
+  const int reduced_tpb = (nmax_sites >= 128 && !o.dense_chains) ? 512 : 256;
+  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : reduced_tpb);
   {
     ctx->boost = (ctx->prec != PQMC_FP64 && o.dense_chains) ? 1 : 0;
     const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb, ctx->boost);

@@ -13,7 +13,10 @@ size_t smem_fixed(int prec) { return prec == 0 ? al16(sizeof(Smem<double>)) : al
 // CTAs per SM a launch is built for: the reduced paths pack twice as many
 // chains per SM as the FP64 path (their FP32 work and the FP64 stabilisation of
 // different chains overlap); smaller CTAs pack more chains.
-int ctas_per_sm(int prec, int tpb, int boost) { return (256 / tpb) * (prec == 0 ? 1 : 2) * (boost ? 2 : 1); }
+int ctas_per_sm(int prec, int tpb, int boost) {
+  if (tpb >= 512) return 1;
+  return (256 / tpb) * (prec == 0 ? 1 : 2) * (boost ? 2 : 1);
+}
 
 // Largest resident footprint a launch offers per chain.
 size_t smem_resident_cap(int prec, int tpb, int boost) {

@@ -93,3 +93,24 @@ def test_theta_convergence_study_runs():
     for row in r["rows"]:
         assert np.isfinite(row["E"]) and np.isfinite(row["s_afm"]) and row["sign"] == 1.0
         assert -1.5 < row["E"] < 0.5 and 0.0 < row["s_afm"] <= 0.25
+
+
+def test_cta_shapes_agree_on_reduced_path():
+    """FP32 sweeps of an uneven batch with 256- and 512-thread CTAs: every
+    product element is the same sequence of FMAs in both shapes, so G and the
+    accept/reject sequences agree exactly; the records agree to rounding of
+    the CTA-wide sums."""
+    specs = [workloads.honeycomb(3, two_theta=2.0, g=0.6, M_N=0.21),
+             workloads.honeycomb(6, two_theta=2.0, g=0.6, M_N=0.21),
+             workloads.honeycomb(9, two_theta=2.0, g=0.6, M_N=0.21)]
+    out = {}
+    for tpb in (256, 512):
+        ctx = pqmc.Context(specs, prec=pqmc.FP32, seed=4, n_stab=2, cta_threads=tpb, accept_log=1 << 16)
+        ctx.sweep(2)
+        out[tpb] = [(ctx.accept_log(2 * (s.n_slices + 2) * s.n_sites, c), ctx.green(c, 0), ctx.measurements(c))
+                    for c, s in enumerate(specs)]
+        ctx.close()
+    for (a0, g0, r0), (a1, g1, r1) in zip(out[256], out[512]):
+        assert np.array_equal(a0, a1)
+        assert np.array_equal(g0, g1)
+        assert np.allclose(r0, r1, rtol=1e-12, atol=1e-14)
