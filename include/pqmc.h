@@ -215,6 +215,40 @@ pqmc_status pqmc_get_fields(pqmc_ctx* ctx, int chain, int8_t* fields);
  * sweeps: G(tau = -1); after an odd number: G(tau = Ltau+1)). */
 pqmc_status pqmc_get_green(pqmc_ctx* ctx, int chain, int spin, double* out);
 
+/* G_sigma at the stabilisation point tau = b * n_stab (b = 0 .. Ltau/n_stab),
+ * recomputed from the chain's current fields by the context's own kernels:
+ * the right stack B_tau ... B_0 P and the left stack P^T B_{Ltau+1} ...
+ * B_{tau+1}, each QR-factorised every n_stab slices, then
+ * G = 1 - B_R (B_L B_R)^{-1} B_L as at a stabilisation (the equal-time Green's
+ * function of the Method section, both Gutzwiller slices included). The
+ * chain's state (stacks, G, counters) is kept aside in a temporary device
+ * buffer and put back, so the Markov chain is not disturbed. out: FP64 N x N row-major. Synchronises.
+ * PQMC_EINVAL for b out of range; PQMC_ENOMEM if the temporary buffer cannot
+ * be allocated. */
+pqmc_status pqmc_get_green_at(pqmc_ctx* ctx, int chain, int spin, int b, double* out);
+
+/* Checkpoint of every chain's Markov-chain state: fields, G, both stacks and
+ * their log-determinants, counters and running sign, measurement records,
+ * stabilisation-error history, accept log, and the sweep index. With
+ * buf == NULL, *len receives the size in bytes and nothing is copied;
+ * otherwise *len is the capacity of buf (PQMC_EINVAL, with *len set to the
+ * size, when it is too small) and on return the bytes written. The caller
+ * owns buf. Synchronises; returns the context's sticky error, if any,
+ * instead of writing. The format is this library's own (a versioned header,
+ * then raw little-endian device contents). */
+pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len);
+
+/* Load a checkpoint into a context created with the same chain specs and the
+ * same precision, n_stab, delay_k, seed, chain_offset, max_meas and
+ * accept_log (cta_threads and dense_chains may differ: they do not change the
+ * results). Later sweeps then continue the checkpointed run exactly: the same
+ * Philox draws, accept decisions, G and records. Clears a sticky
+ * PQMC_ESTAB / PQMC_ENAN / PQMC_ETIMEOUT of the context, so a failed run can
+ * resume from its last good checkpoint. PQMC_EINVAL (nothing loaded) when
+ * the data is not a checkpoint of this library or was taken from a context
+ * that differs in any of the above. Synchronises. */
+pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len);
+
 /* log|det(B_L B_R)| and sign per spin at the last stabilisation of a chain:
  * out[0..3] = (logabs_up, sign_up, logabs_dn, sign_dn). */
 pqmc_status pqmc_get_weight(pqmc_ctx* ctx, int chain, double* out);

@@ -22,7 +22,7 @@
 namespace pqmc {
 size_t smem_resident_cap(int prec, int tpb, int boost);
 cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
-                        size_t res, int* d_err, cudaStream_t stream);
+                        size_t res, int* d_err, cudaStream_t stream, int b_at);
 cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res);
 cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains, int n, uint64_t seed,
                          uint32_t* sweep_ctr, int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
@@ -426,7 +426,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int), ctx->stream);
   if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->res_bytes);
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
-  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
+  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream, -1);
   ctx->launches++;
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "init launch"); }
   pqmc_status st = sync_check(ctx);
@@ -451,6 +451,69 @@ pqmc_status read_records(pqmc_ctx* ctx, int chain, std::vector<double>& rec, int
   if (n == 0) return PQMC_OK;
   cudaError_t e = cudaMemcpy(rec.data(), ctx->desc[chain].meas, rec.size() * 8, cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "record copy");
+}
+
+// Device regions of the arena that hold one chain's Markov-chain state.
+// stacks_only: what a recomputation of G from the fields overwrites (G, the
+// stacks, their log-determinants, the counters); otherwise also the fields,
+// the measurement records, the stabilisation-error history, the accept log
+// and the latest record. Model tables, trial orbitals and the phase scratch
+// are not state: they are rebuilt at creation or rewritten before use.
+struct Region { size_t off, bytes; };
+
+std::vector<Region> chain_state_regions(const pqmc_ctx* ctx, int c, bool stacks_only) {
+  const HostChain& h = ctx->chains[c];
+  const size_t blk = (size_t)h.N * h.nmax * 8;
+  std::vector<Region> r = {{h.off_G, 2ull * h.N * h.ld * ctx->tsize},
+                           {h.off_Rst, (size_t)(h.nb + 1) * 2 * blk},
+                           {h.off_Lst, (size_t)(h.nb + 1) * 2 * blk},
+                           {h.off_Rlog, (size_t)(h.nb + 1) * 4 * 8},
+                           {h.off_Llog, (size_t)(h.nb + 1) * 4 * 8},
+                           {h.off_state, sizeof(ChainState)}};
+  if (!stacks_only) {
+    r.push_back({h.off_fields, (size_t)(h.Ltau + 2) * h.nfld});
+    r.push_back({h.off_meas, (size_t)ctx->opts.max_meas * kRecord * 8});
+    r.push_back({h.off_dG, (size_t)kDGHistory * 8});
+    r.push_back({h.off_acc, (size_t)ctx->opts.accept_log});
+    r.push_back({ctx->off_last + (size_t)c * kRecord * 8, (size_t)kRecord * 8});
+  }
+  return r;
+}
+
+// Checkpoint layout: this header, then every chain's state regions in the
+// order of chain_state_regions, chain by chain (little-endian, as on the
+// device).
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, n_chains;
+  int32_t prec, n_stab, delay_k, max_meas, accept_log, chain_offset;
+  uint64_t seed, spec_hash, payload;
+  uint32_t sweep_index, pad;
+};
+constexpr char kCkptMagic[8] = {'P', 'Q', 'M', 'C', 'C', 'K', 'P', 0};
+
+// FNV-1a over the quantities that fix each chain's layout and dynamics
+uint64_t spec_hash(const pqmc_ctx* ctx) {
+  uint64_t hsh = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) { hsh ^= b[i]; hsh *= 1099511628211ull; }
+  };
+  for (const HostChain& h : ctx->chains) {
+    const pqmc_chain_spec& s = h.spec;
+    const int iv[] = {s.lattice.kind, s.lattice.Lx, s.lattice.Ly, h.N, h.nup, h.ndn, h.Ltau, h.nfld};
+    const double dv[] = {s.lattice.t, s.lattice.tp, s.U, s.dtau, s.two_theta, s.trial.g, s.trial.M_N, s.trial.tiebreak};
+    mix(iv, sizeof iv);
+    mix(dv, sizeof dv);
+  }
+  return hsh;
+}
+
+size_t checkpoint_payload(const pqmc_ctx* ctx) {
+  size_t t = 0;
+  for (int c = 0; c < (int)ctx->chains.size(); ++c)
+    for (const Region& r : chain_state_regions(ctx, c, false)) t += r.bytes;
+  return t;
 }
 
 // ratio estimate sum(s O)/sum(s) with a jackknife over the given groups
@@ -636,7 +699,8 @@ pqmc_status pqmc_set_fields(pqmc_ctx* ctx, int chain, const int8_t* fields) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fields upload");
-  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->res_bytes, ctx->d_err, ctx->stream);
+  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->res_bytes, ctx->d_err,
+                  ctx->stream, -1);
   ctx->launches++;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "init launch");
   return sync_check(ctx);
@@ -667,6 +731,122 @@ pqmc_status pqmc_get_green(pqmc_ctx* ctx, int chain, int spin, double* out) {
       out[(size_t)i * h.N + j] = ctx->tsize == 8 ? reinterpret_cast<double*>(buf.data())[k]
                                                  : (double)reinterpret_cast<float*>(buf.data())[k];
     }
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_get_green_at(pqmc_ctx* ctx, int chain, int spin, int b, double* out) {
+  if (!chain_ok(ctx, chain) || !out || spin < 0 || spin > 1) return PQMC_EINVAL;
+  const HostChain& h = ctx->chains[chain];
+  if (b < 0 || b > h.nb) return fail(ctx, PQMC_EINVAL, "stabilisation point out of range");
+  if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
+  pqmc_status st = sync_check(ctx);
+  if (st != PQMC_OK) return st;
+  // keep the chain's state aside, recompute, read G, put the state back
+  const std::vector<Region> regs = chain_state_regions(ctx, chain, true);
+  size_t total = 0;
+  for (const Region& r : regs) total += r.bytes;
+  unsigned char* keep = nullptr;
+  cudaError_t e = cudaMalloc(&keep, total);
+  if (e != cudaSuccess) return fail(ctx, PQMC_ENOMEM, std::string("state copy: ") + cudaGetErrorString(e));
+  size_t at = 0;
+  for (const Region& r : regs) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(keep + at, ctx->d_arena + r.off, r.bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    at += r.bytes;
+  }
+  if (e == cudaSuccess)
+    e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, chain, 1, ctx->opts.seed, ctx->res_bytes, ctx->d_err,
+                    ctx->stream, b);
+  ctx->launches++;
+  if (e != cudaSuccess) { cudaStreamSynchronize(ctx->stream); cudaFree(keep); return cuda_fail(ctx, e, "recompute launch"); }
+  st = sync_check(ctx);
+  if (st == PQMC_OK) st = pqmc_get_green(ctx, chain, spin, out);
+  at = 0;
+  e = cudaSuccess;
+  for (const Region& r : regs) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_arena + r.off, keep + at, r.bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    at += r.bytes;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(keep);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "state restore");
+  return st;
+}
+
+pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx || !len) return PQMC_EINVAL;
+  if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
+  pqmc_status st = sync_check(ctx);
+  if (st != PQMC_OK) return st;
+  const size_t payload = checkpoint_payload(ctx);
+  const size_t total = sizeof(CkptHeader) + payload;
+  if (!buf) { *len = total; return PQMC_OK; }
+  if (*len < total) { *len = total; return fail(ctx, PQMC_EINVAL, "checkpoint buffer too small"); }
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kCkptMagic, sizeof hd.magic);
+  hd.version = 1;
+  hd.n_chains = (uint32_t)ctx->chains.size();
+  hd.prec = ctx->prec;
+  hd.n_stab = ctx->opts.n_stab;
+  hd.delay_k = ctx->opts.delay_k;
+  hd.max_meas = ctx->opts.max_meas;
+  hd.accept_log = ctx->opts.accept_log;
+  hd.chain_offset = ctx->opts.chain_offset;
+  hd.seed = ctx->opts.seed;
+  hd.spec_hash = spec_hash(ctx);
+  hd.payload = payload;
+  hd.sweep_index = ctx->sweep_index;
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  memcpy(p, &hd, sizeof hd);
+  size_t at = sizeof hd;
+  for (int c = 0; c < (int)ctx->chains.size(); ++c)
+    for (const Region& r : chain_state_regions(ctx, c, false)) {
+      if (r.bytes) {
+        cudaError_t e = cudaMemcpy(p + at, ctx->d_arena + r.off, r.bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "checkpoint copy");
+      }
+      at += r.bytes;
+    }
+  *len = total;
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx || !buf) return PQMC_EINVAL;
+  CkptHeader hd;
+  if (len < sizeof hd) return fail(ctx, PQMC_EINVAL, "not a checkpoint (too short)");
+  memcpy(&hd, buf, sizeof hd);
+  if (memcmp(hd.magic, kCkptMagic, sizeof hd.magic) != 0 || hd.version != 1)
+    return fail(ctx, PQMC_EINVAL, "not a checkpoint of this library");
+  const char* what = nullptr;
+  if (hd.n_chains != (uint32_t)ctx->chains.size()) what = "chain count";
+  else if (hd.prec != ctx->prec) what = "precision";
+  else if (hd.n_stab != ctx->opts.n_stab || hd.delay_k != ctx->opts.delay_k) what = "n_stab or delay_k";
+  else if (hd.max_meas != ctx->opts.max_meas || hd.accept_log != ctx->opts.accept_log) what = "max_meas or accept_log";
+  else if (hd.chain_offset != ctx->opts.chain_offset || hd.seed != ctx->opts.seed) what = "seed or chain_offset";
+  else if (hd.spec_hash != spec_hash(ctx)) what = "chain specs";
+  else if (hd.payload != checkpoint_payload(ctx) || len != sizeof hd + hd.payload) what = "size";
+  if (what) return fail(ctx, PQMC_EINVAL, std::string("checkpoint of a different context: ") + what);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  const unsigned char* p = static_cast<const unsigned char*>(buf);
+  size_t at = sizeof hd;
+  for (int c = 0; c < (int)ctx->chains.size(); ++c)
+    for (const Region& r : chain_state_regions(ctx, c, false)) {
+      if (r.bytes) {
+        e = cudaMemcpy(ctx->d_arena + r.off, p + at, r.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "restore copy");
+      }
+      at += r.bytes;
+    }
+  // the sweep index (host and device copies) and a clean error word: the
+  // checkpoint was taken without an error, so the chains run on from it
+  const int words[2] = {0, (int)hd.sweep_index};
+  e = cudaMemcpy(ctx->d_err, words, sizeof words, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "restore copy");
+  ctx->sweep_index = hd.sweep_index;
+  ctx->sticky = PQMC_OK;
+  ctx->err.clear();
   return PQMC_OK;
 }
 

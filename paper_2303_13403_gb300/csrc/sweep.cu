@@ -37,10 +37,10 @@ cudaError_t launch_advance(uint32_t* sweep_ctr, int n, cudaStream_t stream) {
 }
 
 cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
-                        size_t res, int* d_err, cudaStream_t stream) {
-  if (prec == 0) return launch_init_f64(tpb, d_chains, chain0, n, seed, res, d_err, stream);
-  if (boost) return launch_init_f32_dense(tpb, d_chains, chain0, n, seed, res, d_err, stream);
-  return launch_init_f32(tpb, d_chains, chain0, n, seed, res, d_err, stream);
+                        size_t res, int* d_err, cudaStream_t stream, int b_at) {
+  if (prec == 0) return launch_init_f64(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
+  if (boost) return launch_init_f32_dense(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
+  return launch_init_f32(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
 }
 
 cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res) {
@@ -232,7 +232,7 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
     const size_t cap = smem_resident_cap(0, 256, 0);
     const size_t rb = resident_bytes(N, ld, nmax, 8);
     e = launch_init_t<double, 256, 1>(reinterpret_cast<const ChainDesc*>(base + o_desc), 0, 1, 0,
-                                      rb <= cap ? rb : 0, reinterpret_cast<int*>(base + o_err), st_);
+                                      rb <= cap ? rb : 0, reinterpret_cast<int*>(base + o_err), st_, -1);
   }
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(d_G, (size_t)N * 8, base + o_G, (size_t)ld * 8, (size_t)N * 8, 2 * (size_t)N,

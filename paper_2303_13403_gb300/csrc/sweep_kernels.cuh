@@ -1562,20 +1562,28 @@ __device__ void write_back(Cta<T>& x) {
   __syncthreads();
 }
 
+// b_at < 0: initialisation from the chain's fields (left stack, right block
+// 0, G at tau = -1 and the running sign). b_at >= 0: the left stack down to
+// block b_at, the right stack up to it and G at the stabilisation point
+// tau = b_at * n_stab, all from the fields (a recomputation the host wraps
+// in a save and restore of the chain's state).
 template <typename T, int TPB, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) init_kernel(const ChainDesc* chains, int chain0, uint64_t seed,
-                                                          size_t res_bytes, int* err) {
+                                                          size_t res_bytes, int* err, int b_at) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cta<T> x = make_cta<T>(chains[chain0 + blockIdx.x], smem_raw, res_bytes, seed);
   Smem<T>& sh = x.sh;
   load_state(x);
   const ChainDesc& c = x.c;
-  for (int b = c.nb; b >= 0; --b) push_L(x, b);
-  push_R(x, 0);
-  refresh(x, 0, false);
-  if (threadIdx.x == 0) sh.sign_running = sh.sign_spin[0] * sh.sign_spin[1];
-  __syncthreads();
-  wrap(x, 0, -1);
+  const int bt = b_at < 0 ? 0 : b_at;
+  for (int b = c.nb; b >= bt; --b) push_L(x, b);
+  for (int b = 0; b <= bt; ++b) push_R(x, b);
+  refresh(x, bt, false);
+  if (b_at < 0) {
+    if (threadIdx.x == 0) sh.sign_running = sh.sign_spin[0] * sh.sign_spin[1];
+    __syncthreads();
+    wrap(x, 0, -1);
+  }
   write_back(x);
   store_state(x, err);
 }
@@ -1614,11 +1622,11 @@ static size_t dyn_smem(size_t res) {
 
 template <typename T, int TPB, int MINB>
 static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res, int* d_err,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, int b_at) {
   const size_t sm = dyn_smem<T>(res);
   cudaError_t e = cudaFuncSetAttribute(init_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  init_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, chain0, seed, res, d_err);
+  init_kernel<T, TPB, MINB><<<n, TPB, sm, stream>>>(d_chains, chain0, seed, res, d_err, b_at);
   return cudaGetLastError();
 }
 
@@ -1644,8 +1652,8 @@ static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t see
 // CTA shapes that PQMC_TPB_DISPATCH (defined by the including unit) selects.
 #define PQMC_DEFINE_LAUNCHERS(P)                                                                                  \
   cudaError_t launch_init_##P(int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,    \
-                              int* d_err, cudaStream_t stream) {                                                   \
-    PQMC_TPB_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream);                                \
+                              int* d_err, cudaStream_t stream, int b_at) {                                         \
+    PQMC_TPB_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream, b_at);                          \
   }                                                                                                                \
   cudaError_t prepare_sweep_##P(int tpb, size_t res) { PQMC_TPB_DISPATCH(prepare_sweep_t, res); }                  \
   cudaError_t launch_sweep_##P(int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,      \
@@ -1656,7 +1664,7 @@ static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t see
 // Per-path launchers (one translation unit each).
 #define PQMC_DECLARE_LAUNCHERS(P)                                                                                 \
   cudaError_t launch_init_##P(int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,    \
-                              int* d_err, cudaStream_t stream);                                                    \
+                              int* d_err, cudaStream_t stream, int b_at);                                          \
   cudaError_t prepare_sweep_##P(int tpb, size_t res);                                                              \
   cudaError_t launch_sweep_##P(int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,      \
                                int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);

@@ -68,6 +68,9 @@ SIGNATURES = [
     ("pqmc_set_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int8)]),
     ("pqmc_get_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int8)]),
     ("pqmc_get_green", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    ("pqmc_get_green_at", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    ("pqmc_checkpoint", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("pqmc_restore", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("pqmc_get_weight", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     ("pqmc_get_accept_log", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), C.c_long]),
     ("pqmc_get_stab_errors", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
@@ -200,6 +203,27 @@ class Context:
         out = np.zeros((N, N))
         _check(load().pqmc_get_green(self._h, chain, spin, _dptr(out)), self._h)
         return out
+
+    def green_at(self, b, chain=0, spin=0):
+        """G at the stabilisation point tau = b * n_stab, recomputed from the
+        chain's current fields (the chain's own state is left unchanged)."""
+        N = self.dims(chain)["N"]
+        out = np.zeros((N, N))
+        _check(load().pqmc_get_green_at(self._h, chain, spin, b, _dptr(out)), self._h)
+        return out
+
+    def checkpoint(self):
+        """The state of every chain and the sweep index, as bytes."""
+        n = C.c_size_t(0)
+        _check(load().pqmc_checkpoint(self._h, None, C.byref(n)), self._h)
+        buf = (C.c_ubyte * n.value)()
+        _check(load().pqmc_checkpoint(self._h, buf, C.byref(n)), self._h)
+        return bytes(buf)[: n.value]
+
+    def restore(self, data):
+        """Load a checkpoint taken from a context with the same specs and options."""
+        buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+        _check(load().pqmc_restore(self._h, buf, len(data)), self._h)
 
     def weight(self, chain=0):
         out = np.zeros(4)
