@@ -94,7 +94,9 @@ namespace pqmc {
 
 // Byte offsets of the phase buffers inside one chain's scratch region.  The
 // phases never overlap in time, so their buffers share the region:
-//   wrap    : Gt (N x ld, T) for one spin at a time
+//   wrap    : Gt (N x ld, T) for one spin at a time; for a chain resident in
+//             shared memory also copies of e^{-dtau K} and e^{+dtau K}
+//             (em, ep; 0 when they would make the scratch larger)
 //   flips   : A_S (N x kBlock, T), W and M W (kBlock x ld, T) for one spin,
 //             and the per-block flip buffers
 //   stack   : M64 (N x n, FP64, column-major), then a region holding the two
@@ -105,7 +107,7 @@ namespace pqmc {
 //             path precision (N x n, T); LU pivots / multipliers; O^{-1} in
 //             the path precision (n x n, T)
 struct ScratchLayout {
-  size_t gt, u, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, ot, total;
+  size_t gt, em, ep, u, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, ot, total;
 };
 
 PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -145,6 +147,9 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   if (flush > t) t = flush;
   if (stack > t) t = stack;
   if (refresh > t) t = refresh;
+  L.em = wrap;
+  L.ep = 2 * wrap;
+  if (3 * wrap > t) L.em = L.ep = 0;
   L.total = (t + 255) & ~(size_t)255;
   return L;
 }

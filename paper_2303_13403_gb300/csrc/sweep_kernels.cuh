@@ -741,6 +741,25 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
   const int N = c.N, ld = c.ld;
   const bool gz = x.gutz(tau);
   T* Gt = x.Gt();
+  const T* Em = x.Em();
+  const T* Ep = x.Ep();
+  if (!gz && x.resident && x.L.em) {
+    // a chain resident in shared memory reads e^{-+dtau K} there: the two
+    // tables are copied in from the L2-resident copy shared by all chains
+    // (the wrap phase leaves room for them in the scratch)
+    const int chunks = N * ld * (int)sizeof(T) / 16;
+    int4* dm = reinterpret_cast<int4*>(x.scr + x.L.em);
+    int4* dp = reinterpret_cast<int4*>(x.scr + x.L.ep);
+    const int4* sm = reinterpret_cast<const int4*>(Em);
+    const int4* sp = reinterpret_cast<const int4*>(Ep);
+    for (int e = threadIdx.x; e < chunks; e += blockDim.x) {
+      dm[e] = sm[e];
+      dp[e] = sp[e];
+    }
+    Em = reinterpret_cast<const T*>(dm);
+    Ep = reinterpret_cast<const T*>(dp);
+    __syncthreads();
+  }
   x.stage(tau);
   if (dir > 0) {
     for (int s = 0; s < x.nspec(); ++s) {
@@ -751,17 +770,17 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
     if (gz) return;
     // Gt = e^{-dtau K} G, G = Gt e^{+dtau K}
     for (int s = 0; s < x.nspec(); ++s) {
-      path_gemm<T>(c, N, N, N, x.Em(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
+      path_gemm<T>(c, N, N, N, Em, 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
       __syncthreads();
-      path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Ep(), ld, 1, x.G(s), ld, 1, EpiStore());
+      path_gemm<T>(c, N, N, N, Gt, ld, 1, Ep, ld, 1, x.G(s), ld, 1, EpiStore());
       __syncthreads();
     }
   } else {
     if (!gz) {
       for (int s = 0; s < x.nspec(); ++s) {
-        path_gemm<T>(c, N, N, N, x.Ep(), 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
+        path_gemm<T>(c, N, N, N, Ep, 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
         __syncthreads();
-        path_gemm<T>(c, N, N, N, Gt, ld, 1, x.Em(), ld, 1, x.G(s), ld, 1, EpiStore());
+        path_gemm<T>(c, N, N, N, Gt, ld, 1, Em, ld, 1, x.G(s), ld, 1, EpiStore());
         __syncthreads();
       }
     }
@@ -893,10 +912,14 @@ __device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, do
 // Upper triangle (2 x 2 tiles on or above the diagonal) of C = M^T M for the
 // column-major N x n matrix M (ld N); C row-major n x n.
 static __device__ void gram_upper_f64(int n, int N, const double* M, double* C) {
+  // 2 x 2 output tiles (ti, tj), ti <= tj, enumerated over a flat index so
+  // that every warp carries only tiles of the upper triangle (the FP64 pipe
+  // takes the same time for a partial warp as for a full one)
   const int tn = (n + 1) >> 1;
-  for (int t = threadIdx.x; t < tn * tn; t += blockDim.x) {
-    const int ti = t / tn, tj = t - ti * tn;
-    if (tj < ti) continue;
+  for (int t = threadIdx.x; t < tn * (tn + 1) / 2; t += blockDim.x) {
+    int ti = 0, tj = t;
+    while (tj >= tn - ti) { tj -= tn - ti; ++ti; }
+    tj += ti;
     const int i0 = ti << 1, j0 = tj << 1;
     const double* a0 = M + (long)i0 * N;
     const double* a1 = M + (long)min(i0 + 1, n - 1) * N;
@@ -1117,30 +1140,36 @@ __device__ void gj_invert2(Cta<T>& x, const int n[2], double* O[2], double logab
   x.mark(kPhGJTail);
 }
 
-// C = A^T B for column-major A, B (K x m and K x m', ld K): FP64, 2 x 2
-// outputs per thread, so that small products still occupy every warp.
+// C = A^T B for column-major A, B (K x m and K x m', ld K): FP64, 2 x 3
+// outputs per thread (a 36 x 36 product is 216 tiles: one pass of a
+// 256-thread CTA).
 static __device__ void gemm_tn_f64(int m, int mp, int K, const double* A, const double* B, double* C, int ldc) {
-  const int tm = (m + 1) >> 1, tn = (mp + 1) >> 1;
+  const int tm = (m + 1) >> 1, tn = (mp + 2) / 3;
   for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
-    const int i0 = (t / tn) << 1, j0 = (t % tn) << 1;
+    const int i0 = (t / tn) << 1, j0 = (t % tn) * 3;
     const double* a0 = A + (long)i0 * K;
     const double* a1 = A + (long)min(i0 + 1, m - 1) * K;
     const double* b0 = B + (long)j0 * K;
     const double* b1 = B + (long)min(j0 + 1, mp - 1) * K;
-    double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+    const double* b2 = B + (long)min(j0 + 2, mp - 1) * K;
+    double c00 = 0, c01 = 0, c02 = 0, c10 = 0, c11 = 0, c12 = 0;
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
-      const double x0 = a0[k], x1 = a1[k], y0 = b0[k], y1 = b1[k];
+      const double x0 = a0[k], x1 = a1[k], y0 = b0[k], y1 = b1[k], y2 = b2[k];
       c00 = fma(x0, y0, c00);
       c01 = fma(x0, y1, c01);
+      c02 = fma(x0, y2, c02);
       c10 = fma(x1, y0, c10);
       c11 = fma(x1, y1, c11);
+      c12 = fma(x1, y2, c12);
     }
     C[(long)i0 * ldc + j0] = c00;
     if (j0 + 1 < mp) C[(long)i0 * ldc + j0 + 1] = c01;
+    if (j0 + 2 < mp) C[(long)i0 * ldc + j0 + 2] = c02;
     if (i0 + 1 < m) {
       C[(long)(i0 + 1) * ldc + j0] = c10;
       if (j0 + 1 < mp) C[(long)(i0 + 1) * ldc + j0 + 1] = c11;
+      if (j0 + 2 < mp) C[(long)(i0 + 1) * ldc + j0 + 2] = c12;
     }
   }
 }
