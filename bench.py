@@ -21,6 +21,7 @@ import argparse
 import json
 import multiprocessing as mp
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -68,6 +69,25 @@ def _oracle_worker(args):
         if time.perf_counter() - t0 >= seconds:
             break
     return n * props, time.perf_counter() - t0
+
+
+def cpu_model():
+    """The host CPU as the kernel reports it (model name on x86, the
+    implementer / part codes on Arm), else the machine type."""
+    try:
+        info = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip().lower(), v.strip())
+        if "model name" in info:
+            return info["model name"]
+        if "cpu part" in info:
+            return "%s, CPU implementer %s part %s" % (platform.machine(), info.get("cpu implementer", "?"),
+                                                      info["cpu part"])
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def oracle_rate(two_theta, n_stab, seconds, cores=None):
@@ -260,6 +280,7 @@ def run_ours(a):
         return {"value": ups, "unit": UNIT, "n_stab": NSTAB[name] if not a.n_stab else a.n_stab,
                 "ms_per_step": r["ms"] / steps, "E_per_site": o["E"], "E_err": o["E_err"], "accept": o["accept"],
                 "time_to_sigma_1e-3_s": need / chain_sweeps_per_s,
+                "time_to_sigma_method": "extrapolated from the timed sweeps: t (sigma(E) / 1e-3)^2",
                 "dG_per_stabilisation": {"median": float(np.median(dg)), "p99": float(np.percentile(dg, 99)),
                                          "p999": float(np.percentile(dg, 99.9)), "max": float(dg.max()),
                                          "after": "the first sweep",
@@ -355,6 +376,7 @@ def run_ours(a):
         cs_per_s = rate / props_per_chain
         need = a.chains * a.steps * (res["E_err"] / 1e-3) ** 2
         result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "per_core": rate / cores, "cpu_model": cpu_model(),
                                   "sample": "%d oracle chains (one per core, FP64, n_stab 10), ~%gs of sweeps "
                                             "each, %d updates" % (cores, a.cpu_seconds, n_upd),
                                   "time_to_sigma_1e-3_s": need / cs_per_s}
@@ -389,7 +411,8 @@ def run_reference(a):
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": "gutzwiller_pqmc_honeycomb_6x6_U4_g0.6_MN0.21_2theta%g" % a.two_theta,
                    "sites": 72, "n_stab": n_stab, "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "per_core": value / cores, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
