@@ -97,8 +97,10 @@ namespace pqmc {
 //   wrap    : Gt (N x ld, T) for one spin at a time; for a chain resident in
 //             shared memory also copies of e^{-dtau K} and e^{+dtau K}
 //             (em, ep; 0 when they would make the scratch larger)
-//   flips   : A_S (N x kBlock, T), W and M W (kBlock x ld, T) for one spin,
-//             and the per-block flip buffers
+//   flips   : the update vectors of a block, U (N x kBlock, T) and V
+//             (kBlock x ld, T) of each spin (u, w for spin 0; u2, mw for
+//             spin 1); for t-V blocks A_S (u), W and M W (w, mw); and the
+//             per-block flip buffers
 //   stack   : M64 (N x n, FP64, column-major), then a region holding the two
 //             path-precision product buffers Mt, Mt2 (N x n, T, row-major)
 //             and later the FP64 Q of the QR; Householder betas / R_jj;
@@ -107,7 +109,7 @@ namespace pqmc {
 //             path precision (N x n, T); LU pivots / multipliers; O^{-1} in
 //             the path precision (n x n, T)
 struct ScratchLayout {
-  size_t gt, em, ep, u, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, ot, total;
+  size_t gt, em, ep, u, u2, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, ot, total;
 };
 
 PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -115,7 +117,7 @@ PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 // Per-block buffers of the flip phase (kBlock x kBlock blocks of both spins,
 // ratios, accepted sites); the layout is FlipBuf<T> in sweep_kernels.cuh.
 PQMC_HDI constexpr size_t flipbuf_bytes(int tsize) {
-  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 4 * (size_t)kBlock * tsize + 2 * (size_t)kBlock * 4);
+  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 6 * (size_t)kBlock * tsize + 2 * (size_t)kBlock * 4);
 }
 
 PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
@@ -124,7 +126,8 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
   L.gt = 0;
   size_t wrap = al16((size_t)N * ld * tsize);
   L.u = 0;
-  L.w = al16((size_t)N * kBlock * tsize);
+  L.u2 = al16((size_t)N * kBlock * tsize);
+  L.w = L.u2 + al16((size_t)N * kBlock * tsize);
   L.mw = L.w + al16((size_t)kBlock * ld * tsize);
   L.fb = L.mw + al16((size_t)kBlock * ld * tsize);
   size_t flush = L.fb + flipbuf_bytes(tsize);

@@ -311,6 +311,7 @@ struct FlipBuf {
   T Tu[2][kBlock][kBlock + 1];      // 1 + (1 - G_SS) Gamma, inverted in place, then M
   T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
   T rs[2][kBlock];                  // ratio R_sigma of each proposal of the block
+  T fr[2][kBlock];                  // Delta / R_sigma of each accepted flip
   int sites[kBlock];                // block index of each accepted flip
   int gsite[kBlock];                // its site
 };
@@ -531,6 +532,61 @@ __device__ void flush_block(Cta<T>& x, int a, bool pivot) {
   x.mark(kPhFlush);
 }
 
+// Applies the a accepted flips of a Hubbard block to G as the chain of
+// rank-1 updates they stand for, in acceptance order (the update of one
+// flip at site i with G the G just before it):
+//     G <- G - (e_i - G_{:,i}) (Delta_i / R_i) G_{i,:}.
+// Written as G <- G - U V over the block: column m of U and row m of V are
+// the vectors of flip m, obtained from the block-start G and the earlier
+// vectors (c = G_{:,s_m} - U V_{:,s_m}, r = G_{s_m,:} - U_{s_m,:} V), one
+// step per flip for the two spins at once (half of the CTA each), then one
+// rank-a product per spin.  Same result as the block form of flush_block,
+// without the a x a inverse.
+template <typename T>
+__device__ void flush_block_sm(Cta<T>& x, int a) {
+  const ChainDesc& c = x.c;
+  FlipBuf<T>& fb = *x.fb;
+  const int N = c.N, ld = c.ld;
+  const int half = (int)blockDim.x >> 1;
+  const int s = (int)threadIdx.x >= half ? 1 : 0;
+  const int t = (int)threadIdx.x - s * half;
+  T* Us[2] = {reinterpret_cast<T*>(x.scr + x.L.u), reinterpret_cast<T*>(x.scr + x.L.u2)};
+  T* Vs[2] = {reinterpret_cast<T*>(x.scr + x.L.w), reinterpret_cast<T*>(x.scr + x.L.mw)};
+  if (threadIdx.x < 2 * kBlock) {
+    const int sp = threadIdx.x / kBlock, m = threadIdx.x % kBlock;
+    if (m < a) fb.fr[sp][m] = fb.cl[sp][m] / fb.rs[sp][fb.sites[m]];
+  }
+  __syncthreads();
+  {
+    const T* Gs = x.G(s);
+    T* U = Us[s];
+    T* V = Vs[s];
+    for (int m = 0; m < a; ++m) {
+      const int sm = fb.gsite[m];
+      const T f = fb.fr[s][m];
+      for (int o = t; o < 2 * N; o += half) {
+        if (o < N) {
+          T cv = Gs[(long)o * ld + sm];
+          for (int l = 0; l < m; ++l) cv = fma(-U[(long)l * N + o], V[(long)l * ld + sm], cv);
+          U[(long)m * N + o] = ((o == sm ? T(1) : T(0)) - cv) * f;
+        } else {
+          const int j = o - N;
+          T rv = Gs[(long)sm * ld + j];
+          for (int l = 0; l < m; ++l) rv = fma(-U[(long)l * N + sm], V[(long)l * ld + j], rv);
+          V[(long)m * ld + j] = rv;
+        }
+      }
+      // the two halves step independently: one named barrier per spin
+      if (s == 0) asm volatile("bar.sync 2, %0;" ::"r"(half) : "memory");
+      else asm volatile("bar.sync 3, %0;" ::"r"(half) : "memory");
+    }
+  }
+  __syncthreads();
+  for (int sp = 0; sp < 2; ++sp) path_gemm<T>(c, N, N, a, Us[sp], 1, N, Vs[sp], ld, 1, x.G(sp), ld, 1, EpiSub());
+  __syncthreads();
+  x.mark(kPhFlush);
+}
+
 template <typename T>
 __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const ChainDesc& c = x.c;
@@ -612,7 +668,7 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
     const int a = sh.na;
     if (a == 0) continue;
 
-    flush_block(x, a, false);
+    flush_block_sm(x, a);
   }
 }
 
