@@ -1062,21 +1062,46 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
   x.mark(kPhQR);
   {
     // Q = M R^{-1}, right-looking over the columns of M: q_k = m_k / R_kk,
-    // m_j -= m_k U_kj for j > k (m_k is read only in its own step); a flat
-    // (column jj >= k, row i) index stepped incrementally keeps the warps full
-    const int sq = step / N, sr = step - sq * N;
-    const int t0 = (int)threadIdx.x / N, r0 = (int)threadIdx.x - t0 * N;
-    for (int k = 0; k < n; ++k) {
-      const double sk = isq[k];
-      const double* Uk = U + (long)k * n;
-      int jj = k + t0, i = r0;
-      while (jj < n) {
-        const double mk = M[(long)k * N + i];
-        if (jj == k) Q[(long)k * N + i] = mk * sk;
-        else M[(long)jj * N + i] = fma(-mk, Uk[jj], M[(long)jj * N + i]);
-        i += sr;
-        jj += sq;
-        if (i >= N) { i -= N; ++jj; }
+    // m_j -= m_k U_kj for j > k, in blocks of four columns: each row first
+    // takes its block's own triangle in registers, then one flat pass
+    // applies the block's four updates to the later columns (a barrier pair
+    // per block instead of per column; every element sees the same FMAs in
+    // the same order as column by column)
+    for (int K = 0; K < n; K += 4) {
+      const int kb = min(4, n - K);
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double mv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mv[u] = u < kb ? M[(long)(K + u) * N + i] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < kb) {
+            Q[(long)(K + u) * N + i] = mv[u] * isq[K + u];
+#pragma unroll
+            for (int v = u + 1; v < 4; ++v)
+              if (v < kb) mv[v] = fma(-mv[u], U[(long)(K + u) * n + K + v], mv[v]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < kb) M[(long)(K + u) * N + i] = mv[u];
+      }
+      __syncthreads();
+      const int j0 = K + kb;
+      if (j0 < n) {
+        const int sq = step / N, sr = step - sq * N;
+        const int t0 = (int)threadIdx.x / N, r0 = (int)threadIdx.x - t0 * N;
+        int jj = j0 + t0, i = r0;
+        while (jj < n) {
+          double acc = M[(long)jj * N + i];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (u < kb) acc = fma(-M[(long)(K + u) * N + i], U[(long)(K + u) * n + jj], acc);
+          M[(long)jj * N + i] = acc;
+          i += sr;
+          jj += sq;
+          if (i >= N) { i -= N; ++jj; }
+        }
       }
       __syncthreads();
     }
