@@ -45,7 +45,12 @@ def parse():
     ap.add_argument("--chains", type=int, default=608, help="chains per GPU (two waves of 2 chains per SM)")
     ap.add_argument("--two-theta", type=float, default=8.0)
     ap.add_argument("--n-stab", type=int, default=0, help="0: 2 for fp32 and bf16x3, 10 for fp64")
-    ap.add_argument("--beside-steps", type=int, default=3, help="steps of the other precisions timed beside (0: skip)")
+    ap.add_argument("--beside-steps", type=int, default=1,
+                    help="nonzero: time the other precisions beside the head with the same --steps/--warmup")
+    ap.add_argument("--tts-sweeps", type=int, default=40,
+                    help="sweeps of the time-to-sigma run of every precision (0: skip)")
+    ap.add_argument("--dg-chains", type=int, default=64,
+                    help="chains of the max|G - G_FP64| diagnostic of the reduced paths (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cta-threads", type=int, default=0, help="threads per chain CTA (0: library default)")
@@ -173,16 +178,13 @@ def sweep_flops(N, n, Ltau, n_stab, acc, prec):
 
     Path precision, per interaction slice per spin: wrap 4 N^3, delayed-update
     flush 2 acc N^3, stack slice products 2 N^2 n.  FP64, per stabilisation per
-    spin: QR of the N x n stack block -- Householder with Q formed (FP64 path)
-    4 n^2 (N - n/3), Cholesky QR (reduced paths) N n (n + 1) for the Gram
-    matrix's upper triangle + n^3/3 for the factor + N n^2 for Q = M R^{-1} --
-    then Q_L^T Q_R 2 n^2 N and the Gauss-Jordan inverse 2 n^3."""
+    spin, Ltau / n_stab stabilisations per sweep: the QR of the N x n stack
+    block 2 n^2 (N - n/3), the overlap Q_L^T Q_R 2 n^2 N and its inverse 2 n^3
+    (the method's arithmetic, whatever QR variant the kernel runs; the
+    kernel's Cholesky QR on the reduced paths does more, N n (n + 1) + n^3/3
+    + N n^2, and is not counted)."""
     path = 2 * Ltau * (4 * N ** 3 + 2 * acc * N ** 3 + 2 * N * N * n)
-    if prec == "fp64":
-        qr = 4 * n * n * (N - n / 3)
-    else:
-        qr = N * n * (n + 1) + n ** 3 / 3 + N * n * n
-    stab = (Ltau // n_stab + 1) * 2 * (qr + 2 * n * n * N + 2 * n ** 3)
+    stab = (Ltau // n_stab) * 2 * (2 * n * n * (N - n / 3) + 2 * n * n * N + 2 * n ** 3)
     return path, stab
 
 
@@ -271,20 +273,99 @@ def run_ours(a):
         N, Ltau = r["dims"]["N"], r["dims"]["Ltau"]
         props = (Ltau + 2) * N
         ups = props * a.chains * world * steps / (r["ms"] / 1e3)
-        chain_sweeps_per_s = a.chains * world * steps / (r["ms"] / 1e3)
         o = r["obs"]
-        # chains are independent and equilibrated: sigma(E) ~ 1/sqrt(chain-sweeps)
-        need = a.chains * world * steps * (o["E_err"] / 1e-3) ** 2 if o["E_err"] == o["E_err"] else float("nan")
-        # (sigma measured from the timed sweeps of every chain, pooled over ranks)
         dg = r["dG"]
         return {"value": ups, "unit": UNIT, "n_stab": NSTAB[name] if not a.n_stab else a.n_stab,
                 "ms_per_step": r["ms"] / steps, "E_per_site": o["E"], "E_err": o["E_err"], "accept": o["accept"],
-                "time_to_sigma_1e-3_s": need / chain_sweeps_per_s,
-                "time_to_sigma_method": "extrapolated from the timed sweeps: t (sigma(E) / 1e-3)^2",
                 "dG_per_stabilisation": {"median": float(np.median(dg)), "p99": float(np.percentile(dg, 99)),
                                          "p999": float(np.percentile(dg, 99.9)), "max": float(dg.max()),
                                          "after": "the first sweep",
-                                         "first_sweep_max": float(r["dG_first"].max())}}
+                                         "first_sweep_max": float(r["dG_first"].max()),
+                                         "against": "G rebuilt from the stacks in the path precision"}}
+
+    def time_to_sigma(name, n_sweeps):
+        """Wall time to sigma(E/site) = 1e-3, warm-up included (the survey's
+        definition): a fresh context of the bench's chains runs n_sweeps
+        measured sweeps, each timed with CUDA events on the context's
+        stream.  The warm-up length is the shortest of 2, 4, 8, 12, 16 sweeps
+        after which the pooled E/site of the first and second halves of the
+        remaining sweeps agree within 2 sigma; sigma after k further sweeps
+        is the jackknife over chains of the per-chain averages of those k
+        sweeps; the time is that of the warm-up plus the first k whose sigma
+        reaches 1e-3 (extrapolated as t (sigma / 1e-3)^2 past the end of the
+        run, and flagged)."""
+        ns = a.n_stab or NSTAB[name]
+        ctx = pqmc.Context(specs, prec=PRECS[name], seed=7, n_stab=ns, chain_offset=rank * a.chains,
+                           max_meas=n_sweeps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_sweeps + 1)]
+        ev[0].record(stream)
+        for k in range(n_sweeps):
+            ctx.sweep(1, measure=True)
+            ev[k + 1].record(stream)
+        ev[-1].synchronize()
+        ctx.synchronize()
+        t_cum = np.array([0.0] + [ev[0].elapsed_time(e) / 1e3 for e in ev[1:]])
+        recs = np.stack([ctx.measurements(c, cap=n_sweeps + 1) for c in range(a.chains)])  # chains x sweeps x 6
+        ctx.close()
+
+        def pooled(r):
+            sums = distributed.chain_sums(list(r))
+            if world > 1:
+                sums = distributed.gather_sums(sums)
+            return distributed.pooled_estimate(sums)
+
+        w_eq, halves = None, None
+        for w in (2, 4, 8, 12, 16):
+            rest = n_sweeps - w
+            if rest < 4:
+                break
+            h1, h2 = pooled(recs[:, w:w + rest // 2]), pooled(recs[:, w + rest // 2:])
+            halves = (h1["E"], h1["E_err"], h2["E"], h2["E_err"])
+            if abs(h1["E"] - h2["E"]) <= 2 * np.hypot(h1["E_err"], h2["E_err"]):
+                w_eq = w
+                break
+        equilibrated = w_eq is not None
+        if w_eq is None:
+            w_eq = min(16, n_sweeps // 2)
+        t_tts, k_hit, sig = None, None, None
+        for k in range(2, n_sweeps - w_eq + 1):
+            sig = pooled(recs[:, w_eq:w_eq + k])["E_err"]
+            if sig <= 1e-3:
+                k_hit = k
+                t_tts = t_cum[w_eq + k]
+                break
+        final = pooled(recs[:, w_eq:])
+        if k_hit is None:
+            sig = final["E_err"]
+            t_tts = t_cum[w_eq] + (t_cum[-1] - t_cum[w_eq]) * (sig / 1e-3) ** 2
+        return {"seconds": float(t_tts), "extrapolated": k_hit is None,
+                "warmup_sweeps": int(w_eq), "equilibrated": bool(equilibrated),
+                "measured_sweeps_to_sigma": k_hit, "sweeps_run": n_sweeps,
+                "ms_per_sweep": float(1e3 * t_cum[-1] / n_sweeps),
+                "E_per_site": final["E"], "E_err": final["E_err"],
+                "E_halves": halves, "n_stab": ns}
+
+    def dg_vs_fp64(name, chains=64, sweeps=6):
+        """Per-stabilisation max |G - G_FP64| with G_FP64 assembled in FP64 from
+        the FP64 factors (opts.dg_fp64), over `chains` chains; the first sweep,
+        which starts from the random initial fields, is reported apart."""
+        ns = a.n_stab or NSTAB[name]
+        ctx = pqmc.Context([spec] * chains, prec=PRECS[name], seed=3, n_stab=ns, stream=stream.cuda_stream,
+                           dg_fp64=1)
+        ctx.sweep(sweeps, measure=False)
+        ctx.synchronize()
+        d = ctx.dims(0)
+        per_sweep = d["Ltau"] // d["n_stab"] + 1
+        hist = [ctx.stab_errors(c, cap=4096) for c in range(chains)]
+        ctx.close()
+        errs = np.concatenate([h[per_sweep:] for h in hist])
+        first = np.concatenate([h[:per_sweep] for h in hist])
+        return {"median": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
+                "p999": float(np.percentile(errs, 99.9)), "max": float(errs.max()),
+                "frac_above_1e-4": float(np.mean(errs > 1e-4)), "stabilisations": int(errs.size),
+                "after": "the first sweep", "first_sweep_max": float(first.max()),
+                "sample": "%d chains x %d sweeps, n_stab %d" % (chains, sweeps, ns),
+                "against": "G_FP64 = 1 - Q_R (Q_L^T Q_R)^-1 Q_L^T assembled in FP64 from the FP64 factors"}
 
     head = a.prec
     n_stab = a.n_stab or NSTAB[head]
@@ -295,13 +376,30 @@ def run_ours(a):
     updates = props_per_chain * a.chains * world * a.steps
     ms = r["ms"]
 
+    # the other precisions, timed beside the head for context with the same
+    # warm-up and step count
     beside = {}
     if a.beside_steps > 0:
         for name in PRECS:
             if name == head:
                 continue
-            rb = timed(name, NSTAB[name], a.beside_steps, 2)
-            beside[name + "_gpu"] = summary(name, rb, a.beside_steps)
+            rb = timed(name, NSTAB[name], a.steps, a.warmup)
+            beside[name + "_gpu"] = summary(name, rb, a.steps)
+
+    # time-to-sigma of every precision, same procedure and sweep budget
+    tts = {}
+    if a.tts_sweeps > 0:
+        for name in PRECS:
+            tts[name] = time_to_sigma(name, a.tts_sweeps)
+        ref = tts.get("fp64")
+        if ref:
+            for name, v in tts.items():
+                v["dE_vs_fp64_sigma"] = (v["E_per_site"] - ref["E_per_site"]) / float(
+                    np.hypot(v["E_err"], ref["E_err"])) if name != "fp64" else 0.0
+    dg64 = {}
+    if a.dg_chains > 0 and rank == 0:
+        for name in ("fp32", "bf16x3"):
+            dg64[name] = dg_vs_fp64(name, chains=a.dg_chains)
 
     # end to end through the public API with host buffers: context creation
     # (host model set-up + upload of the arena from host memory) and, every
@@ -353,9 +451,16 @@ def run_ours(a):
                    "parallelism": "chains%d" % world},
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
-        "time_to_sigma_1e-3_s": res["time_to_sigma_1e-3_s"],
+        "time_to_sigma_1e-3_s": tts[head]["seconds"] if head in tts else None,
+        "time_to_sigma": tts,
+        "time_to_sigma_method": ("wall time on the GPU from the first sweep of a fresh context, warm-up "
+                                 "included, until the jackknife-over-chains sigma(E/site) reaches 1e-3; the "
+                                 "warm-up is the shortest of 2/4/8/12/16 sweeps after which the two halves of "
+                                 "the remaining sweeps agree within 2 sigma; every precision runs the same "
+                                 "procedure with %d sweeps of %d chains" % (a.tts_sweeps, a.chains)),
         "E_per_site": res["E_per_site"], "E_err": res["E_err"], "accept": res["accept"],
         "dG_per_stabilisation": res["dG_per_stabilisation"],
+        "dG_vs_fp64_per_stabilisation": dg64,
         "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": fp64_achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "sweep_kernel",
                      "pipe": "fp64",
@@ -374,12 +479,19 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rate, cores, n_upd = oracle_rate(a.two_theta, NSTAB["fp64"], a.cpu_seconds)
         cs_per_s = rate / props_per_chain
-        need = a.chains * a.steps * (res["E_err"] / 1e-3) ** 2
+        # chain-sweeps the FP64 GPU arm needed for sigma = 1e-3 (warm-up
+        # included), at the oracle's chain-sweep rate on all host cores
+        ref = tts.get("fp64")
+        need = (a.chains * (ref["warmup_sweeps"] + (ref["measured_sweeps_to_sigma"] or
+                                                     (ref["sweeps_run"] - ref["warmup_sweeps"]) *
+                                                     (ref["E_err"] / 1e-3) ** 2))) if ref else None
         result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "per_core": rate / cores, "cpu_model": cpu_model(),
                                   "sample": "%d oracle chains (one per core, FP64, n_stab 10), ~%gs of sweeps "
                                             "each, %d updates" % (cores, a.cpu_seconds, n_upd),
-                                  "time_to_sigma_1e-3_s": need / cs_per_s}
+                                  "time_to_sigma_1e-3_s": need / cs_per_s if need else None,
+                                  "time_to_sigma_method": "the chain-sweeps the FP64 GPU arm needed, at the "
+                                                          "oracle's chain-sweep rate on these cores"}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -40,10 +40,11 @@
  * keeps no reference after the call returns.
  *
  * Errors: every entry point returns a pqmc_status; nothing is thrown across
- * the ABI and the library never aborts. After PQMC_ESTAB, PQMC_ENAN or
- * PQMC_ETIMEOUT the context keeps the error (sticky) and refuses further
- * sweeps; pqmc_last_error() gives a one-line reason. Entry points that read
- * results synchronise the context's stream first.
+ * the ABI and the library never aborts. After PQMC_ESTAB or PQMC_ENAN the
+ * context keeps the error (sticky) and refuses further sweeps and
+ * checkpoints until pqmc_restore loads a good checkpoint; pqmc_last_error()
+ * gives a one-line reason. Entry points that read results synchronise the
+ * context's stream first.
  */
 #ifndef PQMC_H
 #define PQMC_H
@@ -62,7 +63,8 @@ typedef enum {
     PQMC_ECUDA = 3,     /* a CUDA call failed (launch, copy, no device) */
     PQMC_ESTAB = 4,     /* singular matrix in the stabilisation (zero pivot / zero column) */
     PQMC_ENAN = 5,      /* NaN or Inf in a ratio or in G */
-    PQMC_ETIMEOUT = 6   /* a bounded device-side wait gave up */
+    PQMC_ETIMEOUT = 6   /* reserved, never returned: the kernels wait on nothing but
+                           their own CTA barriers, so no device-side wait can time out */
 } pqmc_status;
 
 /* Arithmetic of the wrap and delayed-update products. The stabilisation
@@ -140,6 +142,12 @@ typedef struct {
                                (FP64: 256/cta_threads per SM, others twice that) */
     int dense_chains;       /* reduced paths only: kernels built for twice as many chains per SM
                                (fewer registers per thread); needs cta_threads 64 or 128 */
+    int dg_fp64;            /* reduced paths only, diagnostic: nonzero makes the error recorded at
+                               each stabilisation max |G - G_FP64|, the propagated G against
+                               G_FP64 = 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T assembled in FP64 from the
+                               FP64 factors (instead of against the G refreshed in the path
+                               precision). Costs two extra FP64 products per stabilisation;
+                               changes nothing else (same decisions, same G) */
 } pqmc_opts;
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
@@ -243,8 +251,8 @@ pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len);
  * accept_log (cta_threads and dense_chains may differ: they do not change the
  * results). Later sweeps then continue the checkpointed run exactly: the same
  * Philox draws, accept decisions, G and records. Clears a sticky
- * PQMC_ESTAB / PQMC_ENAN / PQMC_ETIMEOUT of the context, so a failed run can
- * resume from its last good checkpoint. PQMC_EINVAL (nothing loaded) when
+ * PQMC_ESTAB / PQMC_ENAN of the context, so a failed run can resume from
+ * its last good checkpoint. PQMC_EINVAL (nothing loaded) when
  * the data is not a checkpoint of this library or was taken from a context
  * that differs in any of the above. Synchronises. */
 pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len);
@@ -258,7 +266,10 @@ pqmc_status pqmc_get_weight(pqmc_ctx* ctx, int chain, double* out);
 pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);
 
 /* max |G - G_fresh| at each stabilisation, oldest first, up to *n values
- * (in: capacity, out: written). The history keeps the last 4096 values. */
+ * (in: capacity, out: written): the propagated G just before the
+ * stabilisation against the G rebuilt from the stacks (in the path
+ * precision, or in FP64 when opts.dg_fp64 is set). The history keeps the
+ * last 4096 values. */
 pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n);
 
 /* SM clock cycles one chain's CTA has spent, as seen by its thread 0, in
@@ -305,6 +316,27 @@ pqmc_status pqmc_host_model(const pqmc_lattice* lattice, double dtau, const pqmc
  * eigenvalues ascending into w, eigenvectors as columns of V (row-major).
  * Exposed for tests. */
 pqmc_status pqmc_host_eigh(int n, const double* A, double* w, double* V);
+
+/* Error bar of the sign-reweighted estimator <s O>/<s> of the Method
+ * section, as pqmc_measure computes it: the records are split into n_groups
+ * groups (bins of consecutive sweeps of one chain, or whole chains when
+ * pooling), group g contributing the sums sO[g] = sum s O and s[g] = sum s.
+ * mean = sum_g sO[g] / sum_g s[g]; the delete-one-group jackknife takes
+ * r_g = (sum sO - sO[g]) / (sum s - s[g]) and
+ * err = sqrt((n_groups - 1) / n_groups * sum_g (r_g - mean_g r)^2), NaN for
+ * n_groups < 2.  Host arrays of n_groups doubles; no GPU needed (exposed for
+ * tests).  PQMC_EINVAL for n_groups < 1 or a NULL pointer. */
+pqmc_status pqmc_host_jackknife(int n_groups, const double* sO, const double* s, double* mean, double* err);
+
+/* Test hook for the failure path: marks chain `chain` as failed with
+ * `code` (PQMC_ENAN or PQMC_ESTAB) exactly as a sweep kernel that met a NaN
+ * or a singular pivot would, by writing the kernels' error bits into the
+ * chain's device counters and into the context's device error word from the
+ * host.  No kernel runs and no GPU fault is involved.  The next
+ * pqmc_synchronize / pqmc_sweep / pqmc_checkpoint returns `code` and the
+ * context stays failed until pqmc_restore.  Synchronises.  PQMC_EINVAL for a
+ * bad chain index or code. */
+pqmc_status pqmc_inject_error(pqmc_ctx* ctx, int chain, int code);
 
 /* Allocation-free initialisation of one chain.
  *

@@ -5,8 +5,10 @@
 // and drives the sweep kernels (sweep_kernels.cuh, dispatched by sweep.cu) on
 // the context's stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -33,6 +35,13 @@ using namespace pqmc;
 namespace {
 
 thread_local std::string g_init_error;
+
+// NVTX range for the duration of a scope (shows the host-side entry points on
+// a profiler timeline; no effect without a tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct HostChain {
   pqmc_chain_spec spec;
@@ -176,17 +185,15 @@ pqmc_status sync_check(pqmc_ctx* ctx) {
   e = cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "error word copy");
   if (herr) {
-    if (herr & kErrTimeout) ctx->sticky = PQMC_ETIMEOUT;
-    else if (herr & kErrNaN) ctx->sticky = PQMC_ENAN;
-    else ctx->sticky = PQMC_ESTAB;
-    ctx->err = (herr & kErrNaN) ? "NaN or Inf in a ratio or in G" :
-               (herr & kErrStab) ? "singular matrix in the stabilisation" : "device wait timed out";
+    ctx->sticky = (herr & kErrNaN) ? PQMC_ENAN : PQMC_ESTAB;
+    ctx->err = (herr & kErrNaN) ? "NaN or Inf in a ratio or in G" : "singular matrix in the stabilisation";
     return (pqmc_status)ctx->sticky;
   }
   return PQMC_OK;
 }
 
 pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_ctx** out) {
+  NvtxRange range("pqmc_init");
   if (!out) return fail(nullptr, PQMC_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 1 || !specs || !opts) return fail(nullptr, PQMC_EINVAL, "need n >= 1, specs and opts");
@@ -385,6 +392,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.tc = ctx->prec == PQMC_BF16X3 ? 1 : 0;
     d.tv = is_tv(s) ? 1 : 0;
     d.nfld = h.nfld;
+    d.dg64 = (ctx->prec != PQMC_FP64 && o.dg_fp64) ? 1 : 0;
     d.U = s.U;
     const double kap[2] = {hs_coupling(s.dtau * s.U), hs_coupling(s.trial.g)};
     for (int k = 0; k < 2; ++k)
@@ -516,15 +524,11 @@ size_t checkpoint_payload(const pqmc_ctx* ctx) {
   return t;
 }
 
-// ratio estimate sum(s O)/sum(s) with a jackknife over the given groups
-void estimate(const std::vector<std::vector<double>>& groups_sO, const std::vector<std::vector<double>>& groups_s,
-              double& mean, double& err) {
-  const size_t nb = groups_s.size();
-  std::vector<double> so(nb, 0.0), ss(nb, 0.0);
+// ratio estimate sum(s O)/sum(s) with a delete-one-group jackknife error over
+// groups given by their sums so[g] = sum s O, ss[g] = sum s
+void jackknife(size_t nb, const double* so, const double* ss, double& mean, double& err) {
   double tso = 0, tss = 0;
   for (size_t b = 0; b < nb; ++b) {
-    for (double v : groups_sO[b]) so[b] += v;
-    for (double v : groups_s[b]) ss[b] += v;
     tso += so[b];
     tss += ss[b];
   }
@@ -537,6 +541,20 @@ void estimate(const std::vector<std::vector<double>>& groups_sO, const std::vect
   double v = 0;
   for (size_t b = 0; b < nb; ++b) v += (jk[b] - m) * (jk[b] - m);
   err = std::sqrt((double)(nb - 1) / nb * v);
+}
+
+// the same over groups of records; the mean is taken over every record
+// (all_sO / all_s), the error over the groups
+void estimate(const std::vector<std::vector<double>>& groups_sO, const std::vector<std::vector<double>>& groups_s,
+              double all_sO, double all_s, double& mean, double& err) {
+  const size_t nb = groups_s.size();
+  std::vector<double> so(nb, 0.0), ss(nb, 0.0);
+  for (size_t b = 0; b < nb; ++b) {
+    for (double v : groups_sO[b]) so[b] += v;
+    for (double v : groups_s[b]) ss[b] += v;
+  }
+  jackknife(nb, so.data(), ss.data(), mean, err);
+  mean = all_sO / all_s;
 }
 
 }  // namespace
@@ -563,6 +581,7 @@ pqmc_status pqmc_init_batch(int n, const pqmc_chain_spec* specs, const pqmc_opts
 }
 
 pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
+  NvtxRange range("pqmc_sweep");
   if (!ctx || n_sweeps < 0) return PQMC_EINVAL;
   if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
   if (n_sweeps == 0) return PQMC_OK;
@@ -595,11 +614,13 @@ pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
 }
 
 pqmc_status pqmc_synchronize(pqmc_ctx* ctx) {
+  NvtxRange range("pqmc_synchronize");
   if (!ctx) return PQMC_EINVAL;
   return sync_check(ctx);
 }
 
 pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
+  NvtxRange range("pqmc_measure");
   if (!ctx || !out || chain < -1 || chain >= (int)ctx->chains.size()) return PQMC_EINVAL;
   pqmc_status s = sync_check(ctx);
   if (s != PQMC_OK) return s;
@@ -655,13 +676,23 @@ pqmc_status pqmc_measure(pqmc_ctx* ctx, int chain, pqmc_obs* out) {
     out->s_afm = out->s_afm_err = NAN;
     return PQMC_OK;
   }
-  estimate(bE, bs, out->E, out->E_err);
-  estimate(bD, bs, out->docc, out->docc_err);
-  estimate(bS, bs, out->s_afm, out->s_afm_err);
+  // means over every record (a single chain's tail beyond the last full bin
+  // included), errors over the groups
+  double tot_s = 0, tot_E = 0, tot_D = 0, tot_S = 0;
+  for (size_t c = 0; c < per_s.size(); ++c)
+    for (size_t m = 0; m < per_s[c].size(); ++m) {
+      tot_s += per_s[c][m];
+      tot_E += per_E[c][m];
+      tot_D += per_D[c][m];
+      tot_S += per_S[c][m];
+    }
+  estimate(bE, bs, tot_E, tot_s, out->E, out->E_err);
+  estimate(bD, bs, tot_D, tot_s, out->docc, out->docc_err);
+  estimate(bS, bs, tot_S, tot_s, out->s_afm, out->s_afm_err);
   // average sign: mean of s with the same grouping
   std::vector<std::vector<double>> ones;
   for (auto& g : bs) ones.emplace_back(g.size(), 1.0);
-  estimate(bs, ones, out->sign, out->sign_err);
+  estimate(bs, ones, tot_s, (double)nm, out->sign, out->sign_err);
   return PQMC_OK;
 }
 
@@ -735,6 +766,7 @@ pqmc_status pqmc_get_green(pqmc_ctx* ctx, int chain, int spin, double* out) {
 }
 
 pqmc_status pqmc_get_green_at(pqmc_ctx* ctx, int chain, int spin, int b, double* out) {
+  NvtxRange range("pqmc_get_green_at");
   if (!chain_ok(ctx, chain) || !out || spin < 0 || spin > 1) return PQMC_EINVAL;
   const HostChain& h = ctx->chains[chain];
   if (b < 0 || b > h.nb) return fail(ctx, PQMC_EINVAL, "stabilisation point out of range");
@@ -773,6 +805,7 @@ pqmc_status pqmc_get_green_at(pqmc_ctx* ctx, int chain, int spin, int b, double*
 }
 
 pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len) {
+  NvtxRange range("pqmc_checkpoint");
   if (!ctx || !len) return PQMC_EINVAL;
   if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
   pqmc_status st = sync_check(ctx);
@@ -812,6 +845,7 @@ pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len) {
 }
 
 pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len) {
+  NvtxRange range("pqmc_restore");
   if (!ctx || !buf) return PQMC_EINVAL;
   CkptHeader hd;
   if (len < sizeof hd) return fail(ctx, PQMC_EINVAL, "not a checkpoint (too short)");
@@ -958,6 +992,26 @@ pqmc_status pqmc_host_model(const pqmc_lattice* lattice, double dtau, const pqmc
     if (P) memcpy(P, Pm.data(), Pm.size() * 8);
     if (gap) *gap = g;
   }
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_host_jackknife(int n_groups, const double* sO, const double* s, double* mean, double* err) {
+  if (n_groups < 1 || !sO || !s || !mean || !err) return fail(nullptr, PQMC_EINVAL, "bad argument");
+  jackknife((size_t)n_groups, sO, s, *mean, *err);
+  return PQMC_OK;
+}
+
+pqmc_status pqmc_inject_error(pqmc_ctx* ctx, int chain, int code) {
+  if (!chain_ok(ctx, chain) || (code != PQMC_ENAN && code != PQMC_ESTAB)) return PQMC_EINVAL;
+  const int bits = code == PQMC_ENAN ? kErrNaN : kErrStab;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  // the chain's own error word (the sweep kernel skips a failed chain) and
+  // the context-wide word that sync_check reads, as a failing kernel sets them
+  e = cudaMemcpy(reinterpret_cast<unsigned char*>(ctx->desc[chain].st) + offsetof(ChainState, err), &bits,
+                 sizeof bits, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->d_err, &bits, sizeof bits, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "error word copy");
   return PQMC_OK;
 }
 

@@ -21,7 +21,7 @@ enum : int {
 };
 
 // error bits written by the kernels
-enum : int { kErrNaN = 1, kErrStab = 2, kErrTimeout = 4 };
+enum : int { kErrNaN = 1, kErrStab = 2 };
 
 // Mutable per-chain counters, in device memory.
 struct ChainState {
@@ -50,6 +50,8 @@ struct ChainDesc {
   int tc;                  // 1: wrap and delayed-update GEMMs as split BF16 tensor-core products
   int tv;                  // 1: spinless t-V model (one species, bond fields)
   int nfld;                // fields per slice: N, or 3N/2 bonds (tv)
+  int dg64;                // reduced paths: record max |G - G_FP64| (G_FP64 assembled in FP64) at
+                           // each stabilisation instead of the path-precision comparison
   double U;
   double delta[2][2][2];   // [0 Hubbard, 1 Gutzwiller][spin][s=+1 -> 0, s=-1 -> 1]: e^{-2 sigma kappa s} - 1
   double vexp[2][2][2];    // same indexing: e^{sigma kappa s}

@@ -1375,8 +1375,26 @@ struct EpiFresh {
   }
 };
 
+// Epilogue of the FP64 diagnostic assembly: g = delta_ij - v in FP64 against
+// the propagated G (read only).
+template <typename T>
+struct EpiDiff64 {
+  const T* G;
+  int ld;
+  double* dmax;
+  template <typename A, typename TC> __device__ void operator()(TC*, int, int, int i, int j, A v) const {
+    const double g = (i == j ? 1.0 : 0.0) - (double)v;
+    const double d = fabs((double)G[(long)i * ld + j] - g);
+    *dmax = d > *dmax ? d : *dmax;
+  }
+};
+
 // G <- 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T at stabilisation point b; records
 // max |G - G_fresh| when record != 0, and the weight's log|det| and sign.
+// With c.dg64 (reduced paths) the recorded error is max |G - G_FP64|, the
+// propagated G against the same formula assembled in FP64 from the FP64
+// factors; the G that replaces the propagated one is still the
+// path-precision assembly, so the chain itself is unchanged.
 template <typename T>
 __device__ void refresh(Cta<T>& x, int b, bool record) {
   const ChainDesc& c = x.c;
@@ -1384,6 +1402,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
   const int N = c.N, ld = c.ld;
   T* Y = x.Yb();
   T dmax = T(0);
+  double dmax64 = 0.0;
   double sign_total = 1.0;
   int n[2] = {x.nsig(0), x.nsig(1)};
   double* O[2] = {x.Ob(0), x.Ob(1)};
@@ -1401,6 +1420,17 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     const T* qr = reinterpret_cast<const T*>(QR[s]);
     const T* ql = reinterpret_cast<const T*>(QL[s]);
     if constexpr (!std::is_same<T, double>::value) {
+      if (c.dg64 && record) {
+        // Y64 = O^{-1} Q_L^T (n x N, FP64, in the space of the path-precision
+        // copies of Q_R and Q_L, which are written after it), then
+        // max |G - (1 - Q_R Y64)| over the propagated G
+        double* y64 = reinterpret_cast<double*>(x.QRt());
+        cta_gemm<double>(n[s], N, n[s], O[s], n[s], 1, QL[s], N, 1, y64, N, 1, EpiStore());
+        __syncthreads();
+        EpiDiff64<T> ed{x.G(s), ld, &dmax64};
+        cta_gemm<double>(N, N, n[s], QR[s], 1, N, y64, N, 1, (double*)nullptr, 0, 0, ed);
+        __syncthreads();
+      }
       T* qrt = x.QRt();
       T* qlt = x.QLt();
       PQMC_FOR_2D(k, 0, n[s], i, 0, N) {
@@ -1438,7 +1468,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
       sh.sign_spin[s] = 1.0;
     }
   x.mark(kPhAssemble);
-  const double dm = cta_max((double)dmax, sh.red);
+  const double dm = cta_max((c.dg64 && record) ? dmax64 : (double)dmax, sh.red);
   if (threadIdx.x == 0) {
     const double dmax = dm;
     if (!isfinite(dmax)) sh.err |= kErrNaN;

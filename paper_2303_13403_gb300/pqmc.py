@@ -36,7 +36,8 @@ class ChainSpec(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("n_stab", C.c_int), ("delay_k", C.c_int), ("prec", C.c_int), ("seed", C.c_uint64),
                 ("n_chains", C.c_int), ("chain_offset", C.c_int), ("accept_log", C.c_int),
-                ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int), ("dense_chains", C.c_int)]
+                ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int), ("dense_chains", C.c_int),
+                ("dg_fp64", C.c_int)]
 
 
 # columns of a measurement record: sign of the weight, E/site, docc/site,
@@ -87,6 +88,9 @@ SIGNATURES = [
     ("pqmc_host_eigh", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("pqmc_green_noalloc", C.c_int, [C.POINTER(ChainSpec), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    ("pqmc_host_jackknife", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("pqmc_inject_error", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
 ]
 
 
@@ -138,12 +142,12 @@ class Context:
     """One libpqmc context: a batch of chains on the GPU."""
 
     def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=0, chain_offset=0, accept_log=0,
-                 max_meas=0, stream=None, cta_threads=0, dense_chains=0):
+                 max_meas=0, stream=None, cta_threads=0, dense_chains=0, dg_fp64=0):
         lib = load()
         specs = list(specs)
         arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
         opts = Opts(n_stab, delay_k, prec, seed, len(specs), chain_offset, accept_log, max_meas,
-                    C.c_void_p(stream) if stream else None, cta_threads, dense_chains)
+                    C.c_void_p(stream) if stream else None, cta_threads, dense_chains, dg_fp64)
         h = C.c_void_p()
         _check(lib.pqmc_init_batch(len(specs), arr, C.byref(opts), C.byref(h)))
         self._h = h
@@ -262,6 +266,10 @@ class Context:
     def launch_count(self):
         return int(load().pqmc_launch_count(self._h))
 
+    def inject_error(self, code, chain=0):
+        """Test hook: mark a chain failed with ENAN or ESTAB from the host."""
+        _check(load().pqmc_inject_error(self._h, chain, code), self._h)
+
 
 def host_model(spec, spin=0):
     """(K, e^{-dtau K}, P_spin, gap) from the library's host model set-up."""
@@ -287,6 +295,16 @@ def host_eigh(A):
     V = np.zeros((n, n))
     _check(lib.pqmc_host_eigh(n, _dptr(A), _dptr(w), _dptr(V)))
     return w, V
+
+
+def host_jackknife(sO, s):
+    """(mean, err) of sum(sO)/sum(s) with the library's delete-one-group
+    jackknife over the groups whose sums are sO[g], s[g]."""
+    sO = np.ascontiguousarray(sO, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    mean, err = C.c_double(), C.c_double()
+    _check(load().pqmc_host_jackknife(len(s), _dptr(sO), _dptr(s), C.byref(mean), C.byref(err)))
+    return mean.value, err.value
 
 
 def green_noalloc(spec, n_stab, d_fields, d_G, d_logw, stream=None):

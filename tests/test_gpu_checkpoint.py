@@ -91,6 +91,36 @@ def test_restored_run_continues_exactly(prec, first, tpb):
     b.close()
 
 
+@pytest.mark.parametrize("code", [pqmc.ENAN, pqmc.ESTAB])
+def test_failed_chain_is_sticky_and_restore_resumes(code):
+    """The failure path, without a GPU fault: one chain is marked failed from
+    the host exactly as a kernel that met a NaN or a singular pivot marks it
+    (pqmc_inject_error). The next synchronisation reports the error; sweeps
+    and checkpoints are then refused with the same code; restoring the last
+    good checkpoint clears it and the resumed run continues the uninterrupted
+    one bit for bit."""
+    kw = dict(prec=pqmc.FP32, seed=8, n_stab=2, accept_log=1 << 16)
+    ref = pqmc.Context(BATCH, **kw)
+    ref.sweep(5)
+    a = pqmc.Context(BATCH, **kw)
+    a.sweep(2)
+    good = a.checkpoint()
+    a.sweep(1)
+    a.inject_error(code, chain=1)
+    for call in (a.synchronize, lambda: a.sweep(1), a.checkpoint, lambda: a.measure(-1)):
+        with pytest.raises(pqmc.PQMCError) as e:
+            call()
+        assert e.value.status == code
+    a.restore(good)
+    a.sweep(3)
+    sr, sa = state_of(ref, 5), state_of(a, 5)
+    for c, (x, y) in enumerate(zip(sr, sa)):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), (c, k)
+    ref.close()
+    a.close()
+
+
 def test_restore_refuses_other_contexts():
     kw = dict(prec=pqmc.FP32, seed=5, n_stab=2)
     a = pqmc.Context(BATCH, **kw)

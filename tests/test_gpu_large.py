@@ -1,0 +1,96 @@
+"""Oracle parity where the large configurations run (GPU, through the C-ABI).
+
+Chains of 162, 288 and 648 sites keep G in global memory; the reduced paths
+run them on 512-thread CTAs.  After each whole sweep the GPU's G is compared,
+element by element, with the oracle's definition of the equal-time Green's
+function (Method section: G = 1 - B_R (B_L B_R)^{-1} B_L, products
+re-orthonormalised after every slice) on the GPU's own final fields: FP64 to
+1e-10 relative, FP32 to 1e-4 absolute.  At 162 sites the FP64 accept/reject
+sequence of two sweeps is also compared with an oracle chain run from the
+same Philox stream."""
+import numpy as np
+import pytest
+
+from oracle import pqmc as opq
+from paper_2303_13403_gb300 import pqmc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    torch.cuda.set_device(0)
+    pqmc.load()
+
+
+def oracle_params(spec, **kw):
+    base = dict(kind=spec.kind, Lx=spec.Lx, Ly=spec.Ly, t=spec.t, tp=spec.tp, U=spec.U, dtau=spec.dtau,
+                two_theta=spec.two_theta, g=spec.g, M_N=spec.M_N, n_up=spec.n_up, n_dn=spec.n_dn,
+                tiebreak=spec.tiebreak)
+    base.update(kw)
+    return opq.Params(**base)
+
+
+def gutz(L, two_theta):
+    return workloads.honeycomb(L, U=4.0, dtau=0.1, two_theta=two_theta, g=0.6, M_N=0.21)
+
+
+CASES = [
+    # (L, 2 Theta, precision, n_stab, sweeps)
+    (9, 4.0, pqmc.FP64, 10, 2),
+    (12, 4.0, pqmc.FP64, 10, 1),
+    (9, 4.0, pqmc.FP32, 2, 2),
+    (12, 4.0, pqmc.FP32, 2, 2),
+    (18, 2.0, pqmc.FP32, 2, 1),
+]
+
+
+@pytest.mark.parametrize("L,two_theta,prec,n_stab,sweeps", CASES)
+def test_sweeps_against_green_definition(L, two_theta, prec, n_stab, sweeps):
+    spec = gutz(L, two_theta)
+    N = spec.n_sites
+    ctx = pqmc.Context([spec], prec=prec, seed=11, n_stab=n_stab)
+    model = opq.Model(oracle_params(spec, n_stab=n_stab))
+    for k in range(1, sweeps + 1):
+        ctx.sweep(1)
+        f = ctx.fields(0)
+        # after an odd number of sweeps the chain sits at tau = Ltau + 1, after
+        # an even number at tau = -1
+        tau = model.Ltau + 1 if k % 2 else -1
+        for s, sg in ((0, 1), (1, -1)):
+            G = ctx.green(0, s)
+            Gd = opq.green_definition(model, f, tau, sg)
+            assert G.shape == (N, N)
+            if prec == pqmc.FP64:
+                err = np.abs(G - Gd).max() / np.abs(Gd).max()
+                assert err < 1e-10, (N, k, s, err)
+            else:
+                err = np.abs(G - Gd).max()
+                assert err < 1e-4, (N, k, s, err)
+        # the trace invariant of the projector: Tr(1 - G_sigma) = N_sigma
+        assert abs(N - np.trace(ctx.green(0, 0)) - N // 2) < (1e-9 if prec == pqmc.FP64 else 1e-3)
+    rec = ctx.measurements(0)
+    assert len(rec) == sweeps and np.all(rec[:, 0] == 1.0) and np.all(np.isfinite(rec))
+    ctx.close()
+
+
+def test_accept_sequence_162_sites_fp64():
+    """Two FP64 sweeps of a 162-site chain (2 Theta = 2): identical accept/reject
+    sequence, G and energies as the oracle chain from the same seed."""
+    spec = gutz(9, 2.0)
+    ctx = pqmc.Context([spec], prec=pqmc.FP64, seed=13, n_stab=10, accept_log=1 << 16)
+    ctx.sweep(2)
+    d = ctx.dims()
+    n = 2 * (d["Ltau"] + 2) * d["N"]
+    gpu_log = ctx.accept_log(n)
+    ch = opq.Chain(oracle_params(spec, n_stab=10, seed=13))
+    ch.run(0, 2)
+    ora_log = np.array([x[3] for x in ch.accept_log], dtype=np.uint8)
+    assert len(ora_log) == n
+    assert np.array_equal(gpu_log, ora_log)
+    for s, sg in ((0, 1), (1, -1)):
+        assert np.abs(ctx.green(0, s) - ch.G[sg]).max() / np.abs(ch.G[sg]).max() < 1e-10
+    rec = ctx.measurements(0)
+    assert np.allclose(rec[:, 1], [m.energy for m in ch.measurements], rtol=0, atol=1e-10)
+    ctx.close()

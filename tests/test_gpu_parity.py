@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import ed, pqmc as opq
-from paper_2303_13403_gb300 import pqmc, workloads
+from paper_2303_13403_gb300 import distributed, pqmc, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -213,3 +213,46 @@ def test_bf16x3_green_and_stabilisation_error():
     errs = np.concatenate([batch.stab_errors(c) for c in range(32)])
     assert len(errs) == 32 * 4 * 21
     assert np.median(errs) < 1e-3 and np.percentile(errs, 99) < 2e-2
+
+
+def test_measure_errors_equal_oracle_estimator():
+    """pqmc_measure's estimates and jackknife errors (one chain: 20 bins of
+    consecutive sweeps, here with a partial last bin; pooled: over chains)
+    equal the oracle's estimator and the pooled estimate on the same records
+    to 1e-12."""
+    ctx = pqmc.Context([SMALL] * 8, prec=pqmc.FP64, seed=31, n_stab=5)
+    ctx.sweep(47, measure=True)
+    for c in (0, 3):
+        rec = ctx.measurements(c)
+        assert len(rec) == 47
+        obs = ctx.measure(c)
+        s = rec[:, 0]
+        for key, col in (("E", 1), ("docc", 2), ("s_afm", 5)):
+            m, e = opq.estimate(rec[:, col], s)
+            assert abs(obs[key] - m) <= 1e-12 * abs(m), key
+            assert e > 0 and abs(obs[key + "_err"] - e) <= 1e-12 * e, key
+    pooled = ctx.measure(-1)
+    est = distributed.pooled_estimate(distributed.chain_sums([ctx.measurements(c) for c in range(8)]))
+    for key in ("E", "docc", "s_afm"):
+        assert abs(pooled[key] - est[key]) <= 1e-12 * abs(est[key]), key
+        assert abs(pooled[key + "_err"] - est[key + "_err"]) <= 1e-12 * est[key + "_err"], key
+    ctx.close()
+
+
+def test_fp64_diagnostic_changes_nothing_but_the_recorded_error():
+    """opts.dg_fp64 makes the reduced paths record max |G - G_FP64| (G_FP64
+    assembled in FP64 from the FP64 factors) at each stabilisation; the chain
+    itself (decisions, G, records) is the same as without it."""
+    spec = workloads.GUTZ_72[4.0]
+    out = {}
+    for dg in (0, 1):
+        ctx = pqmc.Context([spec] * 4, prec=pqmc.FP32, seed=9, n_stab=2, accept_log=1 << 16, dg_fp64=dg)
+        ctx.sweep(3)
+        n = 3 * (spec.n_slices + 2) * spec.n_sites
+        out[dg] = [(ctx.accept_log(n, c), ctx.green(c, 1), ctx.measurements(c), ctx.stab_errors(c))
+                   for c in range(4)]
+        ctx.close()
+    for (a0, g0, r0, e0), (a1, g1, r1, e1) in zip(out[0], out[1]):
+        assert np.array_equal(a0, a1) and np.array_equal(g0, g1) and np.array_equal(r0, r1)
+        assert len(e0) == len(e1) == 3 * 21
+        assert np.all(np.isfinite(e1)) and e1.max() < 1e-2 and not np.array_equal(e0, e1)

@@ -83,16 +83,31 @@ def test_doped_square_signs_consistent():
         assert np.array_equal(rec[:, 0], rec[:, 4])
 
 
-def test_theta_convergence_study_runs():
-    """The Theta-convergence study (three trial states, uneven projection
-    lengths in one context) on the 8-site cluster: every group yields a finite
-    energy and S_AFM in range, with sign +1 at half filling."""
+def test_theta_convergence_study_against_exact_projection():
+    """The Theta-convergence study of Fig. 2 (GP, SD(AFM), SD(NI) trial states,
+    uneven projection lengths in one context) on the 8-site cluster: every
+    (trial, 2 Theta) energy agrees with the exact Trotterised projection of
+    the same trial state (Fock space, same operator order) within 3 sigma,
+    and the three trial states' exact energies differ at the shortest
+    projection, so the check separates them."""
+    from oracle import ed
     from paper_2303_13403_gb300 import convergence
-    r = convergence.run(L=2, Us=(4.0,), two_thetas=(0.4, 1.6), chains=4, n_warm=2, n_meas=10)
-    assert len(r["rows"]) == 3 * 2
+    two_thetas = (0.4, 1.6)
+    r = convergence.run(L=2, Us=(4.0,), two_thetas=two_thetas, chains=48, n_warm=20, n_meas=150, seed=17)
+    assert len(r["rows"]) == 3 * len(two_thetas)
+    exact = {}
     for row in r["rows"]:
-        assert np.isfinite(row["E"]) and np.isfinite(row["s_afm"]) and row["sign"] == 1.0
-        assert -1.5 < row["E"] < 0.5 and 0.0 < row["s_afm"] <= 0.25
+        g, m_n = convergence.trial_params(row["trial"], row["U"])
+        spec = workloads.honeycomb(2, U=row["U"], dtau=0.1, two_theta=row["two_theta"], g=g, M_N=m_n)
+        m = opq.Model(oracle_params(spec, n_stab=2))
+        c = ed.Cluster(m.K, 4, 4, row["U"])
+        Ex, _ = c.trotter_projection(m.P[1], m.P[-1], g, 0.1, m.Ltau)
+        exact[(row["trial"], row["two_theta"])] = Ex / 8
+        assert row["sign"] == 1.0 and 0.0 < row["s_afm"] <= 0.25
+        assert 0 < row["E_err"] < 0.01
+        assert abs(row["E"] - Ex / 8) < 3 * row["E_err"], (row, Ex / 8)
+    short = [exact[(t, 0.4)] for t in convergence.TRIALS]
+    assert max(short) - min(short) > 0.01
 
 
 def test_cta_shapes_agree_on_reduced_path():
