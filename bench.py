@@ -53,7 +53,8 @@ def parse():
                     help="chains of the max|G - G_FP64| diagnostic of the reduced paths (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--cta-threads", type=int, default=0, help="threads per chain CTA (0: library default)")
+    ap.add_argument("--cta-threads", type=int, default=0, help="threads per chain CTA (0: autotuned)")
+    ap.add_argument("--delay-k", type=int, default=0, help="delayed-update block (0: autotuned)")
     return ap.parse_args()
 
 
@@ -193,10 +194,10 @@ def sweep_flops(N, n, Ltau, n_stab, acc, prec):
 # (an FMA-throughput probe on this machine measured 1.2 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 
-# DRAM bytes (read + write) per chain and sweep of the sweep kernel, FP32 path,
-# 72 sites, 2 Theta = 8, 256-thread CTAs: one ncu capture of 304 chains
-# (profiles/sweep_kernel_gutz72_ncu.md), 1050.0 MB per launch / 304.
-DRAM_BYTES_PER_CHAIN_SWEEP = {"fp32": 1049.96e6 / 304}
+# DRAM bytes (read + write) per chain and sweep of the sweep kernel, by
+# (precision, N, Ltau, delayed block, CTA threads), from one ncu capture of
+# that launch shape; empty until the current kernel has been captured.
+DRAM_BYTES_PER_CHAIN_SWEEP = {}
 
 
 def run_ours(a):
@@ -222,9 +223,21 @@ def run_ours(a):
         if world > 1:
             dist.barrier()
 
+    tuned = {}
+
+    def tune(name, n_stab_):
+        # the library's autotuner (delayed block and CTA shape) on this batch;
+        # contexts created with delay_k = 0 then take the cached pick
+        if name not in tuned:
+            tuned[name] = pqmc.autotune(specs, prec=PRECS[name], n_stab=n_stab_, cta_threads=a.cta_threads,
+                                        delay_k=a.delay_k)
+        return tuned[name]
+
     def timed(name, n_stab_, steps, warmup, clocks=False):
+        tune(name, n_stab_)
         ctx = pqmc.Context(specs, prec=PRECS[name], seed=1, n_stab=n_stab_, chain_offset=rank * a.chains,
-                           max_meas=warmup + steps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads)
+                           max_meas=warmup + steps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads,
+                           delay_k=0)
         for _ in range(warmup):
             ctx.sweep(1, measure=False)
         ctx.synchronize()
@@ -265,7 +278,7 @@ def run_ours(a):
         errs = np.concatenate([h[per_sweep:] for h in hist])
         first = np.concatenate([h[:per_sweep] for h in hist])
         out = {"ms": float(t.item()), "clocks": cl, "obs": obs, "launches": ctx.launch_count() - launches0,
-               "dims": d, "dG": errs, "dG_first": first}
+               "dims": d, "dG": errs, "dG_first": first, "launch": ctx.launch()}
         ctx.close()
         return out
 
@@ -276,6 +289,7 @@ def run_ours(a):
         o = r["obs"]
         dg = r["dG"]
         return {"value": ups, "unit": UNIT, "n_stab": NSTAB[name] if not a.n_stab else a.n_stab,
+                "delay_block": r["launch"]["delay_k"], "cta_threads": r["launch"]["cta_threads"],
                 "ms_per_step": r["ms"] / steps, "E_per_site": o["E"], "E_err": o["E_err"], "accept": o["accept"],
                 "dG_per_stabilisation": {"median": float(np.median(dg)), "p99": float(np.percentile(dg, 99)),
                                          "p999": float(np.percentile(dg, 99.9)), "max": float(dg.max()),
@@ -295,8 +309,10 @@ def run_ours(a):
         reaches 1e-3 (extrapolated as t (sigma / 1e-3)^2 past the end of the
         run, and flagged)."""
         ns = a.n_stab or NSTAB[name]
+        tune(name, ns)
         ctx = pqmc.Context(specs, prec=PRECS[name], seed=7, n_stab=ns, chain_offset=rank * a.chains,
-                           max_meas=n_sweeps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads)
+                           max_meas=n_sweeps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads,
+                           delay_k=0)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_sweeps + 1)]
         ev[0].record(stream)
         for k in range(n_sweeps):
@@ -351,7 +367,7 @@ def run_ours(a):
         which starts from the random initial fields, is reported apart."""
         ns = a.n_stab or NSTAB[name]
         ctx = pqmc.Context([spec] * chains, prec=PRECS[name], seed=3, n_stab=ns, stream=stream.cuda_stream,
-                           dg_fp64=1)
+                           dg_fp64=1, delay_k=32)
         ctx.sweep(sweeps, measure=False)
         ctx.synchronize()
         d = ctx.dims(0)
@@ -408,7 +424,7 @@ def run_ours(a):
     barrier()
     t0 = time.perf_counter()
     ctx = pqmc.Context(specs, prec=PRECS[head], seed=2, n_stab=n_stab, chain_offset=rank * a.chains,
-                       max_meas=a.steps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads)
+                       max_meas=a.steps + 1, stream=stream.cuda_stream, cta_threads=a.cta_threads, delay_k=0)
     h2d = ctx.device_bytes()
     rec = np.zeros((a.chains, pqmc.RECORD))
     d2h = 0
@@ -435,8 +451,8 @@ def run_ours(a):
     # time the two pipes need at their peaks, as a fraction of the launch
     bound_s = fp64_f * a.chains / (FP64_PEAK_TFLOPS * 1e12) + (
         path_f * a.chains / (fp32_peak * 1e12) if head != "fp64" else 0.0)
-    traffic = (DRAM_BYTES_PER_CHAIN_SWEEP[head] * a.chains
-               if head in DRAM_BYTES_PER_CHAIN_SWEEP and N == 72 and Ltau == 80 and a.cta_threads in (0, 256)
+    shape_key = (head, N, Ltau, r["launch"]["delay_k"], r["launch"]["cta_threads"])
+    traffic = (DRAM_BYTES_PER_CHAIN_SWEEP[shape_key] * a.chains if shape_key in DRAM_BYTES_PER_CHAIN_SWEEP
                else None)
     result = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -444,7 +460,12 @@ def run_ours(a):
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "fp64": "f64"}[head], "data": "synthetic",
         "config": {"workload": "gutzwiller_pqmc_honeycomb_6x6_U4_g0.6_MN0.21_2theta%g" % a.two_theta,
                    "sites": N, "slices": Ltau + 2, "chains_per_gpu": a.chains, "global_chains": a.chains * world,
-                   "n_stab": n_stab, "delay_block": 32, "precision": head,
+                   "n_stab": n_stab, "delay_block": r["launch"]["delay_k"],
+                   "cta_threads": r["launch"]["cta_threads"], "precision": head,
+                   "autotune": {k: {"pick": [v["delay_k"], v["cta_threads"]],
+                                    "proxy_slices": v["proxy_ltau"],
+                                    "ms_per_sweep": {"k%d_t%d" % (c["delay_k"], c["cta_threads"]): c["ms_per_sweep"]
+                                                     for c in v["candidates"]}} for k, v in tuned.items()},
                    "l2": "state larger than L2 (%.0f MB of chain state per GPU vs 129 MB L2)" %
                          (a.chains * (2 * 2 * N * N * (4 if head != "fp64" else 8)
                                       + 4 * (Ltau // n_stab + 1) * N * (N // 2) * 8) / 1e6),

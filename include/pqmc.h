@@ -126,7 +126,11 @@ typedef struct {
 
 typedef struct {
     int n_stab;             /* slices between QR stabilisations; Ltau/2 must be a multiple */
-    int delay_k;            /* sites per delayed-update block: 32 (0 selects 32) */
+    int delay_k;            /* sites per delayed-update block of the Hubbard chains: 8, 16, 32
+                               or 64 (accepted flips are applied to G once per block), or 0:
+                               autotune (pqmc_autotune; with opts.cta_threads 0 the CTA
+                               shape is tuned too).  t-V chains propose bonds in blocks of
+                               16 whatever delay_k is */
     int prec;               /* pqmc_precision */
     uint64_t seed;          /* Philox key */
     int n_chains;           /* pqmc_init only: identical chains to run (>= 1) */
@@ -146,8 +150,10 @@ typedef struct {
                                each stabilisation max |G - G_FP64|, the propagated G against
                                G_FP64 = 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T assembled in FP64 from the
                                FP64 factors (instead of against the G refreshed in the path
-                               precision). Costs two extra FP64 products per stabilisation;
-                               changes nothing else (same decisions, same G) */
+                               precision); 2: the G refreshed in the path precision against
+                               G_FP64 (the accuracy of the refresh itself). Costs two extra FP64
+                               products per stabilisation; changes nothing else (same
+                               decisions, same G) */
 } pqmc_opts;
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
@@ -316,6 +322,56 @@ pqmc_status pqmc_host_model(const pqmc_lattice* lattice, double dtau, const pqmc
  * eigenvalues ascending into w, eigenvectors as columns of V (row-major).
  * Exposed for tests. */
 pqmc_status pqmc_host_eigh(int n, const double* A, double* w, double* V);
+
+/* Result of pqmc_autotune: the pick and every candidate's time. */
+typedef struct {
+    int delay_k;            /* picked delayed-update block (sites) */
+    int cta_threads;        /* picked threads per chain CTA */
+    double ms_per_sweep;    /* the pick's time per sweep of the proxy batch */
+    int proxy_ltau;         /* interaction slices per chain of the proxy batch */
+    int n_candidates;
+    int cand_delay_k[32];
+    int cand_cta_threads[32];
+    double cand_ms[32];     /* ms per sweep of each candidate on the proxy batch (NaN: did not run) */
+    int from_cache;         /* 1: the pick came from the cache, no timing was run */
+} pqmc_tune;
+
+/* Autotuner of the launch shape (no counterpart in the paper: it picks how
+ * the GPU runs the sweep, not what the sweep computes).  For the batch
+ * (n, specs) with opts' precision and n_stab it times every candidate
+ * delayed-update block (8, 16, 32, 64 sites; only opts->delay_k when that is
+ * nonzero) and CTA shape (64/128/256 threads for FP64, 64/128/256/512 for the
+ * reduced paths; only opts->cta_threads when nonzero; 64/128 with
+ * dense_chains) and returns the fastest.  The timing runs on a proxy batch:
+ * the same chains with the projection shortened to proxy_ltau interaction
+ * slices (the smallest multiple of 2 n_stab that is >= 8, or the chain's own
+ * Ltau when shorter), one warm-up and two timed sweeps per candidate (CUDA
+ * events on the context's stream).  The pick is cached per process under a
+ * key made of the precision, n_stab, the fixed options and the multiset of
+ * chain shapes (N, N_up, N_dn, Ltau, model); with the environment variable
+ * PQMC_AUTOTUNE_CACHE naming a file, the cache is also read from and written
+ * to that file as JSON.  pqmc_init / pqmc_init_batch call this when
+ * opts->delay_k is 0.  Allocates a temporary context (device memory).
+ * PQMC_EINVAL for bad specs or options, PQMC_ECUDA when no candidate ran. */
+pqmc_status pqmc_autotune(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_tune* out);
+
+/* Launch shape of a context: out[0..3] = (delayed-update block in sites,
+ * threads per chain CTA, chain CTAs per SM the kernel is built for, shared
+ * memory bytes offered to a chain that keeps G and its scratch resident; a
+ * chain whose footprint is larger keeps them in global memory). */
+pqmc_status pqmc_get_launch(pqmc_ctx* ctx, int* out);
+
+/* Micro-benchmarks of the arithmetic pipes that bound the sweep (no
+ * counterpart in the paper: they measure the GPU the library runs on).  On
+ * the current device: out[0] FP64 FMA TFLOP/s over all SMs, out[1] FP64
+ * tensor-core (mma.sync m8n8k4 f64) TFLOP/s, out[2] FP32 FMA TFLOP/s,
+ * out[3..5] clock cycles of one dependent FP64 FMA, add + divide, and
+ * add + square root, out[6..9] clock cycles per FP64 warp instruction of one
+ * warp with 1, 8, 16 and 32 active lanes (8 independent chains per lane),
+ * out[10] SM count, out[11] the reported SM clock in MHz.  Allocates and
+ * frees a small device buffer; synchronises the device.  PQMC_ECUDA on a
+ * CUDA failure. */
+pqmc_status pqmc_probe_pipes(double* out);
 
 /* Error bar of the sign-reweighted estimator <s O>/<s> of the Method
  * section, as pqmc_measure computes it: the records are split into n_groups

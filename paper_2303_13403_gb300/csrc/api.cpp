@@ -7,11 +7,17 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
+#include <cctype>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -23,6 +29,7 @@
 
 namespace pqmc {
 size_t smem_resident_cap(int prec, int tpb, int boost);
+int ctas_per_sm(int prec, int tpb, int boost);
 cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
                         size_t res, int* d_err, cudaStream_t stream, int b_at);
 cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res);
@@ -72,6 +79,7 @@ struct pqmc_ctx {
   struct GraphEntry { int n_sweeps, measure; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;          // captured (sweep, advance) pairs
   int tpb = 256;                           // threads per chain CTA
+  int scratch_kd = kBlock;                 // delayed block the per-chain scratch is sized for
   int boost = 0;                           // 1: reduced-path kernels built for twice the CTAs per SM
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -192,15 +200,21 @@ pqmc_status sync_check(pqmc_ctx* ctx) {
   return PQMC_OK;
 }
 
-pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_ctx** out) {
+pqmc_status autotune_cached(int n, const pqmc_chain_spec* specs, const pqmc_opts& o, pqmc_tune* out);
+
+bool valid_delay(int k) { return k == 8 || k == 16 || k == 32 || k == 64; }
+
+// scratch_kd: size the per-chain scratch for delayed blocks up to this many
+// sites (the autotuner's proxy context runs every block size on one arena)
+pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_ctx** out,
+                      int scratch_kd = 0) {
   NvtxRange range("pqmc_init");
   if (!out) return fail(nullptr, PQMC_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 1 || !specs || !opts) return fail(nullptr, PQMC_EINVAL, "need n >= 1, specs and opts");
   pqmc_opts o = *opts;
   if (o.prec < PQMC_FP64 || o.prec > PQMC_BF16X3) return fail(nullptr, PQMC_EINVAL, "unknown precision");
-  if (o.delay_k == 0) o.delay_k = kBlock;
-  if (o.delay_k != kBlock) return fail(nullptr, PQMC_EINVAL, "delay_k must be 0 or 32");
+  if (o.delay_k != 0 && !valid_delay(o.delay_k)) return fail(nullptr, PQMC_EINVAL, "delay_k must be 0, 8, 16, 32 or 64");
   if (o.max_meas <= 0) o.max_meas = 4096;
   if (o.accept_log < 0) return fail(nullptr, PQMC_EINVAL, "accept_log < 0");
   if (o.cta_threads != 0 && o.cta_threads != 64 && o.cta_threads != 128 && o.cta_threads != 256 &&
@@ -217,9 +231,20 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
     return fail(nullptr, PQMC_ECUDA, "no CUDA device");
+  if (o.delay_k == 0) {
+    // delay_k = 0: the autotuner picks the delayed block (and the CTA shape
+    // when that is not fixed)
+    pqmc_tune t;
+    const pqmc_status ts = autotune_cached(n, specs, o, &t);
+    if (ts != PQMC_OK) return ts;
+    o.delay_k = t.delay_k;
+    if (o.cta_threads == 0) o.cta_threads = t.cta_threads;
+  }
+  if (scratch_kd < o.delay_k) scratch_kd = o.delay_k;
 
   auto* ctx = new pqmc_ctx();
   ctx->opts = o;
+  ctx->scratch_kd = scratch_kd;
   ctx->prec = o.prec;
   ctx->tsize = o.prec == PQMC_FP64 ? 8 : 4;
 
@@ -294,7 +319,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     h.off_Lst = take((size_t)(h.nb + 1) * 2 * blk);
     h.off_Rlog = take((size_t)(h.nb + 1) * 4 * 8);
     h.off_Llog = take((size_t)(h.nb + 1) * 4 * 8);
-    h.off_scratch = take(scratch_layout(h.N, h.ld, h.nmax, (int)ctx->tsize).total);
+    h.off_scratch = take(scratch_layout(h.N, h.ld, h.nmax, (int)ctx->tsize, scratch_kd).total);
     h.off_meas = take((size_t)o.max_meas * kRecord * 8);
     h.off_dG = take((size_t)kDGHistory * 8);
     h.off_acc = take((size_t)std::max(o.accept_log, 1));
@@ -314,7 +339,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     ctx->boost = (ctx->prec != PQMC_FP64 && o.dense_chains) ? 1 : 0;
     const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb, ctx->boost);
     for (const HostChain& h : ctx->chains) {
-      const size_t r = resident_bytes(h.N, h.ld, h.nmax, (int)ctx->tsize);
+      const size_t r = resident_bytes(h.N, h.ld, h.nmax, (int)ctx->tsize, o.delay_k);
       if (r <= cap && r > ctx->res_bytes) ctx->res_bytes = r;
     }
   }
@@ -392,7 +417,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.tc = ctx->prec == PQMC_BF16X3 ? 1 : 0;
     d.tv = is_tv(s) ? 1 : 0;
     d.nfld = h.nfld;
-    d.dg64 = (ctx->prec != PQMC_FP64 && o.dg_fp64) ? 1 : 0;
+    d.dg64 = (ctx->prec != PQMC_FP64 && (o.dg_fp64 == 1 || o.dg_fp64 == 2)) ? o.dg_fp64 : 0;
     d.U = s.U;
     const double kap[2] = {hs_coupling(s.dtau * s.U), hs_coupling(s.trial.g)};
     for (int k = 0; k < 2; ++k)
@@ -444,6 +469,221 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
 }
 
 bool chain_ok(pqmc_ctx* ctx, int chain) { return ctx && chain >= 0 && chain < (int)ctx->chains.size(); }
+
+// ---------------------------------------------------------------- autotuner
+//
+// Picks the delayed-update block and the CTA shape of a batch by timing
+// every candidate on a proxy of the batch (same chains, shorter projection),
+// all candidates on one proxy context whose scratch is sized for the largest
+// block: the context is re-targeted (block size in every chain descriptor,
+// CTA shape, shared-memory budget) between candidates.
+
+// Point a context at another delayed block and CTA shape.
+pqmc_status retarget(pqmc_ctx* ctx, int kd, int tpb) {
+  ctx->opts.delay_k = kd;
+  ctx->opts.cta_threads = tpb;
+  ctx->tpb = tpb;
+  ctx->res_bytes = 0;
+  const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb, ctx->boost);
+  for (const HostChain& h : ctx->chains) {
+    const size_t r = resident_bytes(h.N, h.ld, h.nmax, (int)ctx->tsize, kd);
+    if (r <= cap && r > ctx->res_bytes) ctx->res_bytes = r;
+  }
+  for (auto& d : ctx->desc) d.kb = kd;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * ctx->desc.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->res_bytes);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+  return e == cudaSuccess ? PQMC_OK : cuda_fail(ctx, e, "retarget");
+}
+
+// ms per sweep of the context as it is set up: one warm-up sweep, then two
+// timed with CUDA events on its stream; NaN when a launch fails
+double time_sweeps(pqmc_ctx* ctx) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NAN;
+  const int n = (int)ctx->chains.size();
+  cudaError_t e = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, n, ctx->opts.seed, ctx->d_sweep, 1, 0,
+                               ctx->res_bytes, ctx->d_err, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    e = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, n, ctx->opts.seed, ctx->d_sweep, 1, 0,
+                     ctx->res_bytes, ctx->d_err, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = NAN;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  else cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->launches += 6;
+  return e == cudaSuccess ? ms / 2.0 : NAN;
+}
+
+int proxy_ltau(int Ltau, int n_stab) {
+  int lp = 2 * n_stab;
+  while (lp < 8) lp += 2 * n_stab;
+  return std::min(lp, Ltau);
+}
+
+// cache key: precision, n_stab, the fixed options and the multiset of shapes
+std::string tune_key(int n, const pqmc_chain_spec* specs, const pqmc_opts& o) {
+  std::map<std::string, int> shapes;
+  for (int c = 0; c < n; ++c) {
+    const pqmc_chain_spec& s = specs[c];
+    const int N = n_sites(s.lattice);
+    const int nup = s.trial.N_up < 0 ? N / 2 : s.trial.N_up;
+    const int ndn = is_tv(s) ? 0 : (s.trial.N_dn < 0 ? N / 2 : s.trial.N_dn);
+    const int Ltau = (int)std::lround(s.two_theta / s.dtau);
+    char buf[96];
+    snprintf(buf, sizeof buf, "%d.%d.%d.%d.%s", N, nup, ndn, Ltau, is_tv(s) ? "tv" : "h");
+    shapes[buf]++;
+  }
+  std::ostringstream k;
+  k << "prec" << o.prec << "/nstab" << o.n_stab << "/k" << o.delay_k << "/cta" << o.cta_threads << "/dense"
+    << o.dense_chains;
+  for (auto& kv : shapes) k << "/" << kv.first << "x" << kv.second;
+  return k.str();
+}
+
+struct TuneEntry { int delay_k, cta_threads; double ms; };
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune;
+bool g_tune_file_read = false;
+
+// the JSON cache: an object of {"key": {"delay_k": k, "cta_threads": t, "ms_per_sweep": m}}
+// entries (whitespace anywhere; keys hold no quotes)
+void tune_file_read(const char* path) {
+  std::ifstream f(path);
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string txt = ss.str();
+  size_t pos = 0;
+  auto field = [](const std::string& obj, const char* name, double& v) {
+    const size_t a = obj.find(std::string("\"") + name + "\"");
+    if (a == std::string::npos) return false;
+    const size_t c = obj.find(':', a);
+    if (c == std::string::npos) return false;
+    v = atof(obj.c_str() + c + 1);
+    return true;
+  };
+  while (true) {
+    const size_t q0 = txt.find('"', pos);
+    if (q0 == std::string::npos) break;
+    const size_t q1 = txt.find('"', q0 + 1);
+    if (q1 == std::string::npos) break;
+    size_t b = q1 + 1;
+    while (b < txt.size() && isspace((unsigned char)txt[b])) ++b;
+    if (b >= txt.size() || txt[b] != ':') { pos = q1 + 1; continue; }
+    ++b;
+    while (b < txt.size() && isspace((unsigned char)txt[b])) ++b;
+    if (b >= txt.size() || txt[b] != '{') { pos = q1 + 1; continue; }
+    const size_t e = txt.find('}', b);
+    if (e == std::string::npos) break;
+    const std::string key = txt.substr(q0 + 1, q1 - q0 - 1), obj = txt.substr(b, e - b + 1);
+    double k = 0, t = 0, m = NAN;
+    if (field(obj, "delay_k", k) && field(obj, "cta_threads", t)) {
+      field(obj, "ms_per_sweep", m);
+      const TuneEntry te{(int)k, (int)t, m >= 0 ? m : NAN};
+      if (valid_delay(te.delay_k) && te.cta_threads > 0 && !g_tune.count(key)) g_tune[key] = te;
+    }
+    pos = e + 1;
+  }
+}
+
+void tune_file_write(const char* path) {
+  std::ofstream f(path, std::ios::trunc);
+  f << "{\n";
+  size_t i = 0;
+  for (auto& kv : g_tune) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "{\"delay_k\": %d, \"cta_threads\": %d, \"ms_per_sweep\": %.6g}", kv.second.delay_k,
+             kv.second.cta_threads, std::isfinite(kv.second.ms) ? kv.second.ms : -1.0);
+    f << "  \"" << kv.first << "\": " << buf << (++i < g_tune.size() ? ",\n" : "\n");
+  }
+  f << "}\n";
+}
+
+pqmc_status autotune_run(int n, const pqmc_chain_spec* specs, const pqmc_opts& o, pqmc_tune* out) {
+  memset(out, 0, sizeof *out);
+  std::vector<int> ks = o.delay_k ? std::vector<int>{o.delay_k} : std::vector<int>{8, 16, 32, 64};
+  std::vector<int> tpbs;
+  if (o.cta_threads) tpbs = {o.cta_threads};
+  else if (o.dense_chains) tpbs = {64, 128};
+  else if (o.prec == PQMC_FP64) tpbs = {64, 128, 256};
+  else tpbs = {64, 128, 256, 512};
+  // proxy batch: the same chains with a shorter projection
+  std::vector<pqmc_chain_spec> proxy(specs, specs + n);
+  int lp_max = 0;
+  for (auto& s : proxy) {
+    const int Ltau = (int)std::lround(s.two_theta / s.dtau);
+    const int lp = proxy_ltau(Ltau, o.n_stab);
+    s.two_theta = lp * s.dtau;
+    lp_max = std::max(lp_max, lp);
+  }
+  pqmc_opts po = o;
+  po.delay_k = ks.back();
+  po.cta_threads = tpbs.front();
+  po.accept_log = 0;
+  po.max_meas = 1;
+  po.dg_fp64 = 0;
+  pqmc_ctx* ctx = nullptr;
+  pqmc_status st = build_ctx(n, proxy.data(), &po, &ctx, kMaxDelay);
+  if (st != PQMC_OK) return st;
+  double best = INFINITY;
+  int nc = 0;
+  for (int tpb : tpbs)
+    for (int k : ks) {
+      double ms = NAN;
+      if (retarget(ctx, k, tpb) == PQMC_OK) ms = time_sweeps(ctx);
+      if (nc < 32) {
+        out->cand_delay_k[nc] = k;
+        out->cand_cta_threads[nc] = tpb;
+        out->cand_ms[nc] = ms;
+        ++nc;
+      }
+      if (ms < best) {
+        best = ms;
+        out->delay_k = k;
+        out->cta_threads = tpb;
+      }
+    }
+  pqmc_free(ctx);
+  out->n_candidates = nc;
+  out->ms_per_sweep = best;
+  out->proxy_ltau = lp_max;
+  if (!std::isfinite(best)) return fail(nullptr, PQMC_ECUDA, "autotune: no candidate ran");
+  return PQMC_OK;
+}
+
+pqmc_status autotune_cached(int n, const pqmc_chain_spec* specs, const pqmc_opts& o, pqmc_tune* out) {
+  const std::string key = tune_key(n, specs, o);
+  const char* path = getenv("PQMC_AUTOTUNE_CACHE");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (path && *path && !g_tune_file_read) {
+      tune_file_read(path);
+      g_tune_file_read = true;
+    }
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      memset(out, 0, sizeof *out);
+      out->delay_k = it->second.delay_k;
+      out->cta_threads = it->second.cta_threads;
+      out->ms_per_sweep = it->second.ms;
+      out->from_cache = 1;
+      return PQMC_OK;
+    }
+  }
+  const pqmc_status st = autotune_run(n, specs, o, out);
+  if (st != PQMC_OK) return st;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = TuneEntry{out->delay_k, out->cta_threads, out->ms_per_sweep};
+  if (path && *path) tune_file_write(path);
+  return PQMC_OK;
+}
 
 pqmc_status read_state(pqmc_ctx* ctx, int chain, ChainState& st) {
   cudaError_t e = cudaMemcpy(&st, ctx->desc[chain].st, sizeof st, cudaMemcpyDeviceToHost);
@@ -578,6 +818,28 @@ pqmc_status pqmc_init(const pqmc_lattice* lattice, double U, double dtau, double
 
 pqmc_status pqmc_init_batch(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_ctx** out) {
   return build_ctx(n, specs, opts, out);
+}
+
+pqmc_status pqmc_autotune(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts, pqmc_tune* out) {
+  NvtxRange range("pqmc_autotune");
+  if (n < 1 || !specs || !opts || !out) return fail(nullptr, PQMC_EINVAL, "need n >= 1, specs, opts and out");
+  if (opts->delay_k != 0 && !valid_delay(opts->delay_k))
+    return fail(nullptr, PQMC_EINVAL, "delay_k must be 0, 8, 16, 32 or 64");
+  for (int c = 0; c < n; ++c) {
+    std::string why;
+    if (check_spec(specs[c], opts->n_stab, why) != PQMC_OK)
+      return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
+  }
+  return autotune_cached(n, specs, *opts, out);
+}
+
+pqmc_status pqmc_get_launch(pqmc_ctx* ctx, int* out) {
+  if (!ctx || !out) return PQMC_EINVAL;
+  out[0] = ctx->opts.delay_k;
+  out[1] = ctx->tpb;
+  out[2] = ctas_per_sm(ctx->prec, ctx->tpb, ctx->boost);
+  out[3] = (int)ctx->res_bytes;
+  return PQMC_OK;
 }
 
 pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {

@@ -5,7 +5,8 @@
 
 namespace pqmc {
 
-constexpr int kBlock = 32;        // sites per delayed-update block (one warp)
+constexpr int kBlock = 32;        // sites per flip-decision sub-block (one warp); t-V bond blocks
+constexpr int kMaxDelay = 64;     // largest delayed-update block (sites whose flips are applied at once)
 constexpr int kMaxN = 1024;       // sites per chain
 constexpr int kMaxSigma = 512;    // particles per spin
 constexpr int kQRParts = 8;       // row chunks of the column dots in the Householder QR
@@ -45,13 +46,14 @@ struct ChainState {
 // leading dimension N.
 struct ChainDesc {
   int N, ld, nup, ndn, nmax;
-  int Ltau, nb, n_stab, kb;
+  int Ltau, nb, n_stab, kb;        // kb: delayed-update block, 8, 16, 32 or 64 sites (Hubbard chains)
   uint32_t chain_index;
   int tc;                  // 1: wrap and delayed-update GEMMs as split BF16 tensor-core products
   int tv;                  // 1: spinless t-V model (one species, bond fields)
   int nfld;                // fields per slice: N, or 3N/2 bonds (tv)
-  int dg64;                // reduced paths: record max |G - G_FP64| (G_FP64 assembled in FP64) at
-                           // each stabilisation instead of the path-precision comparison
+  int dg64;                // reduced paths: 1 record max |G - G_FP64| (G_FP64 assembled in FP64) at
+                           // each stabilisation instead of the path-precision comparison; 2 the
+                           // refreshed G against G_FP64
   double U;
   double delta[2][2][2];   // [0 Hubbard, 1 Gutzwiller][spin][s=+1 -> 0, s=-1 -> 1]: e^{-2 sigma kappa s} - 1
   double vexp[2][2][2];    // same indexing: e^{sigma kappa s}
@@ -99,10 +101,10 @@ namespace pqmc {
 //   wrap    : Gt (N x ld, T) for one spin at a time; for a chain resident in
 //             shared memory also copies of e^{-dtau K} and e^{+dtau K}
 //             (em, ep; 0 when they would make the scratch larger)
-//   flips   : the update vectors of a block, U (N x kBlock, T) and V
-//             (kBlock x ld, T) of each spin (u, w for spin 0; u2, mw for
-//             spin 1); for t-V blocks A_S (u), W and M W (w, mw); and the
-//             per-block flip buffers
+//   flips   : the update vectors of a delayed block, U (N x kw, T) and V
+//             (kw x ld, T) of each spin (u, w for spin 0; u2, mw for
+//             spin 1), kw = max(delayed block, kBlock); for t-V blocks A_S
+//             (u), W and M W (w, mw); and the per-block flip buffers
 //   stack   : M64 (N x n, FP64, column-major), then a region holding the two
 //             path-precision product buffers Mt, Mt2 (N x n, T, row-major)
 //             and later the FP64 Q of the QR; Householder betas / R_jj;
@@ -117,21 +119,27 @@ struct ScratchLayout {
 PQMC_HDI constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 // Per-block buffers of the flip phase (kBlock x kBlock blocks of both spins,
-// ratios, accepted sites); the layout is FlipBuf<T> in sweep_kernels.cuh.
+// ratios of one decision sub-block, Delta and Delta/R of each accepted flip of
+// a delayed block, accepted sites); the layout is FlipBuf<T> in
+// sweep_kernels.cuh.
 PQMC_HDI constexpr size_t flipbuf_bytes(int tsize) {
-  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 6 * (size_t)kBlock * tsize + 2 * (size_t)kBlock * 4);
+  return al16(2 * (size_t)kBlock * (kBlock + 1) * tsize + 2 * (size_t)kBlock * tsize +
+              4 * (size_t)kMaxDelay * tsize + 2 * (size_t)kMaxDelay * 4);
 }
 
-PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
+// kd: the delayed-update block of the chain (its update vectors are sized
+// for max(kd, kBlock) flips)
+PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize, int kd) {
   ScratchLayout L;
   const size_t Nn = (size_t)N * n;
+  const size_t kw = kd > kBlock ? (size_t)kd : (size_t)kBlock;
   L.gt = 0;
   size_t wrap = al16((size_t)N * ld * tsize);
   L.u = 0;
-  L.u2 = al16((size_t)N * kBlock * tsize);
-  L.w = L.u2 + al16((size_t)N * kBlock * tsize);
-  L.mw = L.w + al16((size_t)kBlock * ld * tsize);
-  L.fb = L.mw + al16((size_t)kBlock * ld * tsize);
+  L.u2 = al16((size_t)N * kw * tsize);
+  L.w = L.u2 + al16((size_t)N * kw * tsize);
+  L.mw = L.w + al16(kw * ld * tsize);
+  L.fb = L.mw + al16(kw * ld * tsize);
   size_t flush = L.fb + flipbuf_bytes(tsize);
   L.m64 = 0;
   L.mtq = al16(Nn * 8);
@@ -161,8 +169,8 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize) {
 
 // Shared-memory bytes of a chain that keeps G and its scratch resident
 // (a chain that does not fit keeps only the flip buffers in shared memory).
-PQMC_HDI size_t resident_bytes(int N, int ld, int n, int tsize) {
-  return al16(2 * (size_t)N * ld * tsize) + scratch_layout(N, ld, n, tsize).total;
+PQMC_HDI size_t resident_bytes(int N, int ld, int n, int tsize, int kd) {
+  return al16(2 * (size_t)N * ld * tsize) + scratch_layout(N, ld, n, tsize, kd).total;
 }
 
 }  // namespace pqmc

@@ -128,7 +128,7 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
   const size_t o_rlog = take256(off, (size_t)(nb + 1) * 4 * 8);
   const size_t o_llog = take256(off, (size_t)(nb + 1) * 4 * 8);
   const size_t o_G = take256(off, 2 * (size_t)N * ld * 8);
-  const size_t o_scr = take256(off, scratch_layout(N, ld, nmax, 8).total);
+  const size_t o_scr = take256(off, scratch_layout(N, ld, nmax, 8, kBlock).total);
   if (off > kNoAllocBytes) {
     set_init_error("pqmc_green_noalloc: chain needs " + std::to_string(off) + " bytes, above the 16 MiB maximum");
     return PQMC_EINVAL;
@@ -230,7 +230,7 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
   e = cudaMemcpyAsync(base, h.data(), upload, cudaMemcpyHostToDevice, st_);
   if (e == cudaSuccess) {
     const size_t cap = smem_resident_cap(0, 256, 0);
-    const size_t rb = resident_bytes(N, ld, nmax, 8);
+    const size_t rb = resident_bytes(N, ld, nmax, 8, kBlock);
     e = launch_init_t<double, 256, 1>(reinterpret_cast<const ChainDesc*>(base + o_desc), 0, 1, 0,
                                       rb <= cap ? rb : 0, reinterpret_cast<int*>(base + o_err), st_, -1);
   }

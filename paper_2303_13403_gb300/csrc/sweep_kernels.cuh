@@ -308,12 +308,12 @@ __device__ void path_gemm(const ChainDesc& c, int M, int Nn, int K, const T* A, 
 // Buffers of one flip block (lives in shared memory, see make_cta).
 template <typename T>
 struct FlipBuf {
-  T Tu[2][kBlock][kBlock + 1];      // 1 + (1 - G_SS) Gamma, inverted in place, then M
-  T cl[2][kBlock];                  // Delta of each accepted flip (diagonal of Gamma)
-  T rs[2][kBlock];                  // ratio R_sigma of each proposal of the block
-  T fr[2][kBlock];                  // Delta / R_sigma of each accepted flip
-  int sites[kBlock];                // block index of each accepted flip
-  int gsite[kBlock];                // its site
+  T Tu[2][kBlock][kBlock + 1];      // t-V: 1 + (1 - G_SS) Gamma, inverted in place, then M
+  T rs[2][kBlock];                  // ratio R_sigma of each proposal of the decision sub-block
+  T cl[2][kMaxDelay];               // Delta of each accepted flip of the delayed block (diagonal of Gamma)
+  T fr[2][kMaxDelay];               // Delta / R_sigma of each accepted flip
+  int sites[kMaxDelay];             // (unused slot kept for the layout)
+  int gsite[kMaxDelay];             // site of each accepted flip
 };
 static_assert(sizeof(FlipBuf<double>) <= flipbuf_bytes(8) && sizeof(FlipBuf<float>) <= flipbuf_bytes(4),
               "flip buffer layout");
@@ -532,18 +532,19 @@ __device__ void flush_block(Cta<T>& x, int a, bool pivot) {
   x.mark(kPhFlush);
 }
 
-// Applies the a accepted flips of a Hubbard block to G as the chain of
+// The accepted flips of a Hubbard delayed block, applied to G as the chain of
 // rank-1 updates they stand for, in acceptance order (the update of one
 // flip at site i with G the G just before it):
 //     G <- G - (e_i - G_{:,i}) (Delta_i / R_i) G_{i,:}.
 // Written as G <- G - U V over the block: column m of U and row m of V are
 // the vectors of flip m, obtained from the block-start G and the earlier
 // vectors (c = G_{:,s_m} - U V_{:,s_m}, r = G_{s_m,:} - U_{s_m,:} V), one
-// step per flip for the two spins at once (half of the CTA each), then one
-// rank-a product per spin.  Same result as the block form of flush_block,
-// without the a x a inverse.
+// step per flip for the two spins at once (half of the CTA each)
+// (sm_vectors, for flips m0..m1-1 once their decisions are taken), then one
+// rank-a product per spin (apply_vectors).  Same result as the block form of
+// flush_block, without the a x a inverse.
 template <typename T>
-__device__ void flush_block_sm(Cta<T>& x, int a) {
+__device__ void sm_vectors(Cta<T>& x, int m0, int m1) {
   const ChainDesc& c = x.c;
   FlipBuf<T>& fb = *x.fb;
   const int N = c.N, ld = c.ld;
@@ -552,16 +553,11 @@ __device__ void flush_block_sm(Cta<T>& x, int a) {
   const int t = (int)threadIdx.x - s * half;
   T* Us[2] = {reinterpret_cast<T*>(x.scr + x.L.u), reinterpret_cast<T*>(x.scr + x.L.u2)};
   T* Vs[2] = {reinterpret_cast<T*>(x.scr + x.L.w), reinterpret_cast<T*>(x.scr + x.L.mw)};
-  if (threadIdx.x < 2 * kBlock) {
-    const int sp = threadIdx.x / kBlock, m = threadIdx.x % kBlock;
-    if (m < a) fb.fr[sp][m] = fb.cl[sp][m] / fb.rs[sp][fb.sites[m]];
-  }
-  __syncthreads();
   {
     const T* Gs = x.G(s);
     T* U = Us[s];
     T* V = Vs[s];
-    for (int m = 0; m < a; ++m) {
+    for (int m = m0; m < m1; ++m) {
       const int sm = fb.gsite[m];
       const T f = fb.fr[s][m];
       for (int o = t; o < 2 * N; o += half) {
@@ -582,11 +578,25 @@ __device__ void flush_block_sm(Cta<T>& x, int a) {
     }
   }
   __syncthreads();
+  x.mark(kPhFlush);
+}
+
+template <typename T>
+__device__ void apply_vectors(Cta<T>& x, int a) {
+  const ChainDesc& c = x.c;
+  const int N = c.N, ld = c.ld;
+  T* Us[2] = {reinterpret_cast<T*>(x.scr + x.L.u), reinterpret_cast<T*>(x.scr + x.L.u2)};
+  T* Vs[2] = {reinterpret_cast<T*>(x.scr + x.L.w), reinterpret_cast<T*>(x.scr + x.L.mw)};
   for (int sp = 0; sp < 2; ++sp) path_gemm<T>(c, N, N, a, Us[sp], 1, N, Vs[sp], ld, 1, x.G(sp), ld, 1, EpiSub());
   __syncthreads();
   x.mark(kPhFlush);
 }
 
+// Hubbard slice: delayed blocks of c.kb sites (8, 16, 32 or 64), each
+// decided in sub-blocks of up to kBlock sites (one warp per spin) and then
+// applied to G at once.  Within a delayed block a later sub-block reads its
+// diagonal block of G corrected by the update vectors of the flips already
+// accepted, G_SS - U_S V_S, so every decision sees the current G.
 template <typename T>
 __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const ChainDesc& c = x.c;
@@ -597,78 +607,95 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const int kap = x.gutz(tau) ? 1 : 0;
   int8_t* f = c.fields + (long)tau * c.nfld;
   const T dl[2][2] = {{(T)c.delta[kap][0][0], (T)c.delta[kap][0][1]}, {(T)c.delta[kap][1][0], (T)c.delta[kap][1][1]}};
+  const int kd = c.kb;
+  const int sub = kd < kBlock ? kd : kBlock;
 
-  for (int i0 = 0; i0 < N; i0 += kBlock) {
-    const int nbk = min(kBlock, N - i0);
-    if (warp < 2) {
-      // warp s (spin s): lane q holds column q of the spin's diagonal block in
-      // registers; the two warps exchange the spin ratios through shared
-      // memory once per proposal and take the same decision
-      const int s = warp;
-      T gs[kBlock];
-      const bool colq = lane < nbk;
+  for (int d0 = 0; d0 < N; d0 += kd) {
+    const int d1 = min(d0 + kd, N);
+    int a_done = 0;                                  // flips of the delayed block already accepted
+    for (int i0 = d0; i0 < d1; i0 += sub) {
+      const int nbk = min(sub, d1 - i0);
+      if (warp < 2) {
+        // warp s (spin s): lane q holds column q of the spin's diagonal block in
+        // registers; the two warps exchange the spin ratios through shared
+        // memory once per proposal and take the same decision
+        const int s = warp;
+        T gs[kBlock];
+        const bool colq = lane < nbk;
 #pragma unroll
-      for (int r = 0; r < kBlock; ++r) gs[r] = (colq && r < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + lane] : T(0);
-      // lane j: uniform (in the decision precision) and field of site i0 + j
-      T uj = T(2);
-      int flj = 1;
-      if (colq) {
-        const U4 w = philox4x32_10((uint32_t)(i0 + lane), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
-                                   (uint32_t)(x.seed >> 32));
-        uj = uniform_of<T>(((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11));
-        flj = (int)f[i0 + lane];
-      }
-      int a = 0, bad = 0, nneg = 0;
-      const long long pos0 = sh.acc_pos;
+        for (int r = 0; r < kBlock; ++r) gs[r] = (colq && r < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + lane] : T(0);
+        if (a_done > 0 && colq) {
+          // G_SS - U_S V_S over the vectors of the block's earlier flips
+          const T* U = reinterpret_cast<const T*>(x.scr + (s == 0 ? x.L.u : x.L.u2));
+          const T* V = reinterpret_cast<const T*>(x.scr + (s == 0 ? x.L.w : x.L.mw));
+          for (int l = 0; l < a_done; ++l) {
+            const T vq = V[(long)l * ld + i0 + lane];
 #pragma unroll
-      for (int j = 0; j < kBlock; ++j) {
-        if (j < nbk) {
-          const int si = __shfl_sync(0xffffffffu, flj, j) > 0 ? 0 : 1;
-          const T ds = dl[s][si];
-          const T rs = T(1) + ds * (T(1) - __shfl_sync(0xffffffffu, gs[j], j));
-          if (lane == 0) fb.rs[s][j] = rs;
-          asm volatile("bar.sync 1, 64;" ::: "memory");
-          const T R = fb.rs[0][j] * fb.rs[1][j];
-          const bool acc = __shfl_sync(0xffffffffu, (int)(uj < (R < T(0) ? -R : R)), j) != 0;
-          if (s == 0 && lane == 0) {
-            if (!isfinite(R)) bad = 1;
-            if (pos0 + j < c.acc_cap) c.acc_log[pos0 + j] = acc ? 1 : 0;
-          }
-          if (acc) {
-            // G_rq += c G_rj G_jq for future rows r > j and columns q > j
-            const T y = lane > j ? (ds / rs) * gs[j] : T(0);
-#pragma unroll
-            for (int r = j + 1; r < kBlock; ++r) gs[r] = fma(__shfl_sync(0xffffffffu, gs[r], j), y, gs[r]);
-            if (lane == j) {
-              flj = -flj;
-              if (s == 0) f[i0 + j] = (int8_t)flj;
-            }
-            if (s == 0 && lane == 0) {
-              fb.sites[a] = j;
-              fb.gsite[a] = i0 + j;
-              fb.cl[0][a] = ds;
-              fb.cl[1][a] = dl[1][si];
-              nneg += R < T(0) ? 1 : 0;
-            }
-            ++a;
+            for (int r = 0; r < kBlock; ++r)
+              if (r < nbk) gs[r] = fma(-U[(long)l * N + i0 + r], vq, gs[r]);
           }
         }
+        // lane j: uniform (in the decision precision) and field of site i0 + j
+        T uj = T(2);
+        int flj = 1;
+        if (colq) {
+          const U4 w = philox4x32_10((uint32_t)(i0 + lane), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
+                                     (uint32_t)(x.seed >> 32));
+          uj = uniform_of<T>(((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11));
+          flj = (int)f[i0 + lane];
+        }
+        int a = a_done, bad = 0, nneg = 0;
+        const long long pos0 = sh.acc_pos;
+#pragma unroll
+        for (int j = 0; j < kBlock; ++j) {
+          if (j < nbk) {
+            const int si = __shfl_sync(0xffffffffu, flj, j) > 0 ? 0 : 1;
+            const T ds = dl[s][si];
+            const T rs = T(1) + ds * (T(1) - __shfl_sync(0xffffffffu, gs[j], j));
+            if (lane == 0) fb.rs[s][j] = rs;
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            const T R = fb.rs[0][j] * fb.rs[1][j];
+            const bool acc = __shfl_sync(0xffffffffu, (int)(uj < (R < T(0) ? -R : R)), j) != 0;
+            if (s == 0 && lane == 0) {
+              if (!isfinite(R)) bad = 1;
+              if (pos0 + j < c.acc_cap) c.acc_log[pos0 + j] = acc ? 1 : 0;
+            }
+            if (acc) {
+              // G_rq += c G_rj G_jq for future rows r > j and columns q > j
+              const T y = lane > j ? (ds / rs) * gs[j] : T(0);
+#pragma unroll
+              for (int r = j + 1; r < kBlock; ++r) gs[r] = fma(__shfl_sync(0xffffffffu, gs[r], j), y, gs[r]);
+              if (lane == j) {
+                flj = -flj;
+                if (s == 0) f[i0 + j] = (int8_t)flj;
+              }
+              if (lane == 0) fb.fr[s][a] = ds / rs;
+              if (s == 0 && lane == 0) {
+                fb.gsite[a] = i0 + j;
+                fb.cl[0][a] = ds;
+                fb.cl[1][a] = dl[1][si];
+                nneg += R < T(0) ? 1 : 0;
+              }
+              ++a;
+            }
+          }
+        }
+        if (s == 0 && lane == 0) {
+          sh.na = a;
+          sh.acc_pos = pos0 + nbk;
+          sh.n_prop += nbk;
+          sh.n_acc += a - a_done;
+          if (nneg & 1) sh.sign_running = -sh.sign_running;
+          if (bad) sh.err |= kErrNaN;
+        }
       }
-      if (s == 0 && lane == 0) {
-        sh.na = a;
-        sh.acc_pos = pos0 + nbk;
-        sh.n_prop += nbk;
-        sh.n_acc += a;
-        if (nneg & 1) sh.sign_running = -sh.sign_running;
-        if (bad) sh.err |= kErrNaN;
-      }
+      __syncthreads();
+      x.mark(kPhFlip);
+      const int a = sh.na;
+      if (a > a_done) sm_vectors(x, a_done, a);
+      a_done = a;
     }
-    __syncthreads();
-    x.mark(kPhFlip);
-    const int a = sh.na;
-    if (a == 0) continue;
-
-    flush_block_sm(x, a);
+    if (a_done > 0) apply_vectors(x, a_done);
   }
 }
 
@@ -1420,7 +1447,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     const T* qr = reinterpret_cast<const T*>(QR[s]);
     const T* ql = reinterpret_cast<const T*>(QL[s]);
     if constexpr (!std::is_same<T, double>::value) {
-      if (c.dg64 && record) {
+      if (c.dg64 == 1 && record) {
         // Y64 = O^{-1} Q_L^T (n x N, FP64, in the space of the path-precision
         // copies of Q_R and Q_L, which are written after it), then
         // max |G - (1 - Q_R Y64)| over the propagated G
@@ -1453,6 +1480,18 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     __syncthreads();
     EpiFresh<T> epi{x.G(s), ld, &dmax};
     cta_gemm<T>(N, N, n[s], qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
+    if constexpr (!std::is_same<T, double>::value) {
+      if (c.dg64 == 2 && record) {
+        // the refreshed G itself against G_FP64 (the path-precision copies of
+        // Q_R and Q_L are no longer needed: Y64 takes their space)
+        __syncthreads();
+        double* y64 = reinterpret_cast<double*>(x.QRt());
+        cta_gemm<double>(n[s], N, n[s], O[s], n[s], 1, QL[s], N, 1, y64, N, 1, EpiStore());
+        __syncthreads();
+        EpiDiff64<T> ed{x.G(s), ld, &dmax64};
+        cta_gemm<double>(N, N, n[s], QR[s], 1, N, y64, N, 1, (double*)nullptr, 0, 0, ed);
+      }
+    }
     const double l_tot = c.Rlog[(b * 2 + s) * 2 + 0] + la[s] + c.Llog[(b * 2 + s) * 2 + 0];
     const double s_tot = c.Rlog[(b * 2 + s) * 2 + 1] * sg[s] * c.Llog[(b * 2 + s) * 2 + 1];
     if (threadIdx.x == 0) {
@@ -1678,8 +1717,8 @@ __device__ Cta<T> make_cta(const ChainDesc& cg, unsigned char* smem_raw, size_t 
   }
   const ChainDesc& c = sh.desc;
   const int ts = (int)sizeof(T);
-  const ScratchLayout L = scratch_layout(c.N, c.ld, c.nmax, ts);
-  const bool res = resident_bytes(c.N, c.ld, c.nmax, ts) <= res_bytes;
+  const ScratchLayout L = scratch_layout(c.N, c.ld, c.nmax, ts, c.kb);
+  const bool res = resident_bytes(c.N, c.ld, c.nmax, ts, c.kb) <= res_bytes;
   unsigned char* dyn = smem_raw + al16(sizeof(Smem<T>));
   T* Gp = res ? reinterpret_cast<T*>(dyn) : reinterpret_cast<T*>(c.G);
   unsigned char* scr = res ? dyn + al16(2 * (size_t)c.N * c.ld * ts) : reinterpret_cast<unsigned char*>(c.scratch);

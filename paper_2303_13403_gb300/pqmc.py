@@ -54,6 +54,19 @@ class Obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tune(C.Structure):
+    _fields_ = [("delay_k", C.c_int), ("cta_threads", C.c_int), ("ms_per_sweep", C.c_double),
+                ("proxy_ltau", C.c_int), ("n_candidates", C.c_int), ("cand_delay_k", C.c_int * 32),
+                ("cand_cta_threads", C.c_int * 32), ("cand_ms", C.c_double * 32), ("from_cache", C.c_int)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"delay_k": self.delay_k, "cta_threads": self.cta_threads, "ms_per_sweep": self.ms_per_sweep,
+                "proxy_ltau": self.proxy_ltau, "from_cache": bool(self.from_cache),
+                "candidates": [{"delay_k": self.cand_delay_k[i], "cta_threads": self.cand_cta_threads[i],
+                                "ms_per_sweep": self.cand_ms[i]} for i in range(n)]}
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point
@@ -91,6 +104,9 @@ SIGNATURES = [
     ("pqmc_host_jackknife", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("pqmc_inject_error", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("pqmc_autotune", C.c_int, [C.c_int, C.POINTER(ChainSpec), C.POINTER(Opts), C.POINTER(Tune)]),
+    ("pqmc_get_launch", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    ("pqmc_probe_pipes", C.c_int, [C.POINTER(C.c_double)]),
 ]
 
 
@@ -141,8 +157,10 @@ def chain_spec_of(spec):
 class Context:
     """One libpqmc context: a batch of chains on the GPU."""
 
-    def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=0, chain_offset=0, accept_log=0,
+    def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=32, chain_offset=0, accept_log=0,
                  max_meas=0, stream=None, cta_threads=0, dense_chains=0, dg_fp64=0):
+        """delay_k = 0 lets the library's autotuner pick the delayed-update
+        block (and the CTA shape when cta_threads is 0)."""
         lib = load()
         specs = list(specs)
         arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
@@ -266,6 +284,12 @@ class Context:
     def launch_count(self):
         return int(load().pqmc_launch_count(self._h))
 
+    def launch(self):
+        """(delay_k, cta_threads, CTAs per SM, resident shared-memory bytes per chain)."""
+        out = (C.c_int * 4)()
+        _check(load().pqmc_get_launch(self._h, out), self._h)
+        return dict(zip(("delay_k", "cta_threads", "ctas_per_sm", "resident_bytes"), list(out)))
+
     def inject_error(self, code, chain=0):
         """Test hook: mark a chain failed with ENAN or ESTAB from the host."""
         _check(load().pqmc_inject_error(self._h, chain, code), self._h)
@@ -295,6 +319,31 @@ def host_eigh(A):
     V = np.zeros((n, n))
     _check(lib.pqmc_host_eigh(n, _dptr(A), _dptr(w), _dptr(V)))
     return w, V
+
+
+def autotune(specs, prec=FP64, n_stab=10, delay_k=0, cta_threads=0, dense_chains=0, seed=1):
+    """pqmc_autotune: the fastest (delay_k, cta_threads) for the batch, with
+    every candidate's time on the proxy batch."""
+    lib = load()
+    specs = list(specs)
+    arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
+    opts = Opts(n_stab, delay_k, prec, seed, len(specs), 0, 0, 0, None, cta_threads, dense_chains, 0)
+    t = Tune()
+    _check(lib.pqmc_autotune(len(specs), arr, C.byref(opts), C.byref(t)))
+    return t.as_dict()
+
+
+PROBE_KEYS = ("fp64_fma_tflops", "fp64_dmma_tflops", "fp32_fma_tflops", "fp64_fma_latency_cycles",
+              "fp64_div_latency_cycles", "fp64_sqrt_latency_cycles", "fp64_warp_instr_cycles_1_lane",
+              "fp64_warp_instr_cycles_8_lanes", "fp64_warp_instr_cycles_16_lanes", "fp64_warp_instr_cycles_32_lanes",
+              "sms", "sm_clock_mhz")
+
+
+def probe_pipes():
+    """pqmc_probe_pipes: FP64 / DMMA / FP32 throughput and FP64 latencies of the current GPU."""
+    out = (C.c_double * 12)()
+    _check(load().pqmc_probe_pipes(out))
+    return dict(zip(PROBE_KEYS, list(out)))
 
 
 def host_jackknife(sO, s):

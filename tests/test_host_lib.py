@@ -129,3 +129,22 @@ def test_empty_batch_rejected(lib):
     with pytest.raises(pqmc.PQMCError) as e:
         pqmc.Context([])
     assert e.value.status == pqmc.EINVAL
+
+
+def test_autotune_cache_file_is_read(tmp_path):
+    """The autotuner's JSON cache (PQMC_AUTOTUNE_CACHE): a stored pick for the
+    batch's key is returned without timing anything (so no GPU is needed)."""
+    import json
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.json"
+    key = "prec1/nstab2/k0/cta0/dense0/72.36.36.40.hx4"
+    cache.write_text(json.dumps({key: {"delay_k": 16, "cta_threads": 128, "ms_per_sweep": 1.5}}, indent=1))
+    code = ("import json; from paper_2303_13403_gb300 import pqmc, workloads; "
+            "s = workloads.honeycomb(6, two_theta=4.0, g=0.6, M_N=0.21); "
+            "print(json.dumps(pqmc.autotune([s] * 4, prec=pqmc.FP32, n_stab=2)))")
+    env = dict(os.environ, PQMC_AUTOTUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    t = json.loads(r.stdout.strip().splitlines()[-1])
+    assert t["from_cache"] and t["delay_k"] == 16 and t["cta_threads"] == 128 and t["ms_per_sweep"] == 1.5
