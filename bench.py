@@ -363,25 +363,32 @@ def run_ours(a):
 
     def dg_vs_fp64(name, chains=64, sweeps=6):
         """Per-stabilisation max |G - G_FP64| with G_FP64 assembled in FP64 from
-        the FP64 factors (opts.dg_fp64), over `chains` chains; the first sweep,
-        which starts from the random initial fields, is reported apart."""
+        the FP64 factors (opts.dg_fp64 = 1), and the same divided by
+        max(1, max |G_FP64|) (dg_fp64 = 3), over `chains` chains from one seed
+        (the diagnostic does not change the chain); the first sweep, which
+        starts from the random initial fields, is reported apart."""
         ns = a.n_stab or NSTAB[name]
-        ctx = pqmc.Context([spec] * chains, prec=PRECS[name], seed=3, n_stab=ns, stream=stream.cuda_stream,
-                           dg_fp64=1, delay_k=32)
-        ctx.sweep(sweeps, measure=False)
-        ctx.synchronize()
-        d = ctx.dims(0)
-        per_sweep = d["Ltau"] // d["n_stab"] + 1
-        hist = [ctx.stab_errors(c, cap=4096) for c in range(chains)]
-        ctx.close()
-        errs = np.concatenate([h[per_sweep:] for h in hist])
-        first = np.concatenate([h[:per_sweep] for h in hist])
-        return {"median": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
-                "p999": float(np.percentile(errs, 99.9)), "max": float(errs.max()),
-                "frac_above_1e-4": float(np.mean(errs > 1e-4)), "stabilisations": int(errs.size),
-                "after": "the first sweep", "first_sweep_max": float(first.max()),
-                "sample": "%d chains x %d sweeps, n_stab %d" % (chains, sweeps, ns),
-                "against": "G_FP64 = 1 - Q_R (Q_L^T Q_R)^-1 Q_L^T assembled in FP64 from the FP64 factors"}
+        out = {}
+        for mode, key in ((1, "absolute"), (3, "relative")):
+            ctx = pqmc.Context([spec] * chains, prec=PRECS[name], seed=3, n_stab=ns, stream=stream.cuda_stream,
+                               dg_fp64=mode, delay_k=32)
+            ctx.sweep(sweeps, measure=False)
+            ctx.synchronize()
+            d = ctx.dims(0)
+            per_sweep = d["Ltau"] // d["n_stab"] + 1
+            hist = [ctx.stab_errors(c, cap=4096) for c in range(chains)]
+            ctx.close()
+            errs = np.concatenate([h[per_sweep:] for h in hist])
+            first = np.concatenate([h[:per_sweep] for h in hist])
+            out[key] = {"median": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
+                        "p999": float(np.percentile(errs, 99.9)), "max": float(errs.max()),
+                        "frac_above_1e-4": float(np.mean(errs > 1e-4)), "stabilisations": int(errs.size),
+                        "first_sweep_max": float(first.max())}
+        out["after"] = "the first sweep"
+        out["sample"] = "%d chains x %d sweeps, n_stab %d" % (chains, sweeps, ns)
+        out["against"] = ("G_FP64 = 1 - Q_R (Q_L^T Q_R)^-1 Q_L^T assembled in FP64 from the FP64 factors; "
+                          "relative: divided by max(1, max|G_FP64|) per spin")
+        return out
 
     head = a.prec
     n_stab = a.n_stab or NSTAB[head]

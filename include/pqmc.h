@@ -151,9 +151,10 @@ typedef struct {
                                G_FP64 = 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T assembled in FP64 from the
                                FP64 factors (instead of against the G refreshed in the path
                                precision); 2: the G refreshed in the path precision against
-                               G_FP64 (the accuracy of the refresh itself). Costs two extra FP64
-                               products per stabilisation; changes nothing else (same
-                               decisions, same G) */
+                               G_FP64 (the accuracy of the refresh itself); 3: as 1, divided by
+                               max(1, max |G_FP64|) per spin (the error relative to the size of
+                               G). Costs two extra FP64 products per stabilisation; changes
+                               nothing else (same decisions, same G) */
 } pqmc_opts;
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
@@ -279,11 +280,12 @@ pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);
 pqmc_status pqmc_get_stab_errors(pqmc_ctx* ctx, int chain, double* out, long* n);
 
 /* SM clock cycles one chain's CTA has spent, as seen by its thread 0, in
- * each phase of its sweeps so far: out[0..14] = (flip decisions,
- * delayed-update flushes, slice wrapping, stack slice products, QR
+ * each phase of its sweeps so far: out[0..15] = (flip decisions,
+ * delayed-update products G -= U V, slice wrapping, stack slice products, QR
  * factorisation, rest of the G refresh, measurement, total, forming Q,
- * Q_L^T Q_R, its inverse, G assembly; and inside the inverse: pivot steps,
- * eliminations, column restore and log-determinant). */
+ * Q_L^T Q_R, its inverse, G assembly; inside the inverse: pivot steps,
+ * eliminations, column restore and log-determinant; and the update vectors
+ * U, V of the accepted flips). */
 pqmc_status pqmc_get_phase_cycles(pqmc_ctx* ctx, int chain, long long* out);
 
 /* Sizes of one chain: out[0..6] = (N, N_up, N_dn, Ltau, n_stab, delay_k,

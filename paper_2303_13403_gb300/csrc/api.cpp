@@ -417,7 +417,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.tc = ctx->prec == PQMC_BF16X3 ? 1 : 0;
     d.tv = is_tv(s) ? 1 : 0;
     d.nfld = h.nfld;
-    d.dg64 = (ctx->prec != PQMC_FP64 && (o.dg_fp64 == 1 || o.dg_fp64 == 2)) ? o.dg_fp64 : 0;
+    d.dg64 = (ctx->prec != PQMC_FP64 && o.dg_fp64 >= 1 && o.dg_fp64 <= 3) ? o.dg_fp64 : 0;
     d.U = s.U;
     const double kap[2] = {hs_coupling(s.dtau * s.U), hs_coupling(s.trial.g)};
     for (int k = 0; k < 2; ++k)
@@ -1079,7 +1079,7 @@ pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len) {
   CkptHeader hd;
   memset(&hd, 0, sizeof hd);
   memcpy(hd.magic, kCkptMagic, sizeof hd.magic);
-  hd.version = 1;
+  hd.version = 2;
   hd.n_chains = (uint32_t)ctx->chains.size();
   hd.prec = ctx->prec;
   hd.n_stab = ctx->opts.n_stab;
@@ -1112,7 +1112,7 @@ pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len) {
   CkptHeader hd;
   if (len < sizeof hd) return fail(ctx, PQMC_EINVAL, "not a checkpoint (too short)");
   memcpy(&hd, buf, sizeof hd);
-  if (memcmp(hd.magic, kCkptMagic, sizeof hd.magic) != 0 || hd.version != 1)
+  if (memcmp(hd.magic, kCkptMagic, sizeof hd.magic) != 0 || hd.version != 2)
     return fail(ctx, PQMC_EINVAL, "not a checkpoint of this library");
   const char* what = nullptr;
   if (hd.n_chains != (uint32_t)ctx->chains.size()) what = "chain count";

@@ -16,7 +16,7 @@ constexpr int kDGHistory = 4096;  // stabilisation errors kept per chain
 // phases timed with clock64() by thread 0 of each chain CTA
 enum : int {
   kPhFlip = 0, kPhFlush, kPhWrap, kPhStack, kPhQR, kPhRefresh, kPhMeasure, kPhTotal,
-  kPhQRForm, kPhOverlap, kPhLU, kPhAssemble, kPhGJPivot, kPhGJElim, kPhGJTail, kPhases
+  kPhQRForm, kPhOverlap, kPhLU, kPhAssemble, kPhGJPivot, kPhGJElim, kPhGJTail, kPhFlushVec, kPhases
   // (kPhLU: the marker after the Gauss-Jordan inverse, which the three kPhGJ
   // phases already cover; kept so that the counter layout stays fixed)
 };
@@ -53,7 +53,7 @@ struct ChainDesc {
   int nfld;                // fields per slice: N, or 3N/2 bonds (tv)
   int dg64;                // reduced paths: 1 record max |G - G_FP64| (G_FP64 assembled in FP64) at
                            // each stabilisation instead of the path-precision comparison; 2 the
-                           // refreshed G against G_FP64
+                           // refreshed G against G_FP64; 3 as 1 over max(1, max |G_FP64|)
   double U;
   double delta[2][2][2];   // [0 Hubbard, 1 Gutzwiller][spin][s=+1 -> 0, s=-1 -> 1]: e^{-2 sigma kappa s} - 1
   double vexp[2][2][2];    // same indexing: e^{sigma kappa s}
@@ -110,7 +110,7 @@ namespace pqmc {
 //             and later the FP64 Q of the QR; Householder betas / R_jj;
 //             the Gram matrix and pivots of the Cholesky QR
 //   refresh : O (n x n, FP64, both spins, inverted in place), Y (n x ld, T), Q_R and Q_L in the
-//             path precision (N x n, T); LU pivots / multipliers; O^{-1} in
+//             path precision (N x n, T); GJ pivots / multipliers; O^{-1} in
 //             the path precision (n x n, T)
 struct ScratchLayout {
   size_t gt, em, ep, u, u2, w, mw, fb, m64, mtq, mt2, qaux, chol, o, y, qrt, qlt, laux, ot, total;

@@ -83,15 +83,25 @@ __global__ void dfma_partial(long long* cycles, double* sink, int active, double
   if (threadIdx.x == 0) *cycles = t1 - t0;
 }
 
-// dependent chains on one thread: latency in cycles of FMA, divide, sqrt
+// dependent chains on one thread: latency in cycles of FMA, divide, sqrt.
+// The operations are volatile PTX so that they stay between the clock reads.
 __global__ void dep_latency(long long* cycles, double* sink, double a, double b) {
   double x = 1.0 + threadIdx.x, y = 2.0, z = 3.0;
   long long t0 = clock64();
-  for (int i = 0; i < 256; ++i) x = fma(x, a, b);
+#pragma unroll 1
+  for (int i = 0; i < 256; ++i) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(x) : "d"(a), "d"(b));
   long long t1 = clock64();
-  for (int i = 0; i < 256; ++i) y = a / (y + 1.0);
+#pragma unroll 1
+  for (int i = 0; i < 256; ++i) {
+    asm volatile("add.rn.f64 %0, %0, 0d3FF0000000000000;" : "+d"(y));
+    asm volatile("div.rn.f64 %0, %1, %0;" : "+d"(y) : "d"(a));
+  }
   long long t2 = clock64();
-  for (int i = 0; i < 256; ++i) z = sqrt(z + b);
+#pragma unroll 1
+  for (int i = 0; i < 256; ++i) {
+    asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(z) : "d"(b));
+    asm volatile("sqrt.rn.f64 %0, %0;" : "+d"(z));
+  }
   long long t3 = clock64();
   if (x + y + z == 1.2345) sink[0] = x + y + z;
   cycles[0] = t1 - t0;

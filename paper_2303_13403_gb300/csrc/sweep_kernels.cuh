@@ -578,7 +578,7 @@ __device__ void sm_vectors(Cta<T>& x, int m0, int m1) {
     }
   }
   __syncthreads();
-  x.mark(kPhFlush);
+  x.mark(kPhFlushVec);
 }
 
 template <typename T>
@@ -1409,12 +1409,84 @@ struct EpiDiff64 {
   const T* G;
   int ld;
   double* dmax;
+  double* gmax;      // largest |G_FP64| element
   template <typename A, typename TC> __device__ void operator()(TC*, int, int, int i, int j, A v) const {
     const double g = (i == j ? 1.0 : 0.0) - (double)v;
     const double d = fabs((double)G[(long)i * ld + j] - g);
     *dmax = d > *dmax ? d : *dmax;
+    *gmax = fabs(g) > *gmax ? fabs(g) : *gmax;
   }
 };
+
+// G_fresh = 1 - Q_R X Q_L^T for spin s with X = (Q_L^T Q_R)^{-1} (FP64, n x n
+// row-major at Xinv), in the path precision; the FP64 diagnostics of
+// opts.dg_fp64 around it.
+template <typename T>
+__device__ void assemble_spin(Cta<T>& x, int s, const double* QR, const double* QL, const double* Xinv, int ns,
+                              bool record, T& dmax, double& dmax64) {
+  const ChainDesc& c = x.c;
+  Smem<T>& sh = x.sh;
+  const int N = c.N, ld = c.ld;
+  T* Y = x.Yb();
+  const T* qr = reinterpret_cast<const T*>(QR);
+  const T* ql = reinterpret_cast<const T*>(QL);
+  if constexpr (!std::is_same<T, double>::value) {
+    if ((c.dg64 == 1 || c.dg64 == 3) && record) {
+      // Y64 = O^{-1} Q_L^T (n x N, FP64, in the space of the path-precision
+      // copies of Q_R and Q_L, which are written after it), then
+      // max |G - (1 - Q_R Y64)| over the propagated G (mode 3: divided by
+      // max(1, max |G_FP64|), per spin)
+      double* y64 = reinterpret_cast<double*>(x.QRt());
+      cta_gemm<double>(ns, N, ns, Xinv, ns, 1, QL, N, 1, y64, N, 1, EpiStore());
+      __syncthreads();
+      double d_s = 0.0, g_s = 0.0;
+      EpiDiff64<T> ed{x.G(s), ld, &d_s, &g_s};
+      cta_gemm<double>(N, N, ns, QR, 1, N, y64, N, 1, (double*)nullptr, 0, 0, ed);
+      if (c.dg64 == 3) {
+        d_s = cta_max(d_s, sh.red);
+        g_s = cta_max(g_s, sh.red);
+        d_s /= fmax(1.0, g_s);
+      }
+      dmax64 = fmax(dmax64, d_s);
+      __syncthreads();
+    }
+    T* qrt = x.QRt();
+    T* qlt = x.QLt();
+    PQMC_FOR_2D(k, 0, ns, i, 0, N) {
+      qrt[(long)k * N + i] = (T)QR[(long)k * N + i];
+      qlt[(long)k * N + i] = (T)QL[(long)k * N + i];
+    }
+    qr = qrt;
+    ql = qlt;
+    __syncthreads();
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    cta_gemm<T>(ns, N, ns, Xinv, ns, 1, ql, N, 1, Y, ld, 1, EpiStore());
+  } else {
+    // O^{-1} to the path precision once, then a path-precision product
+    T* ot = x.Ot();
+    for (int e = threadIdx.x; e < ns * ns; e += blockDim.x) ot[e] = (T)Xinv[e];
+    __syncthreads();
+    cta_gemm<T>(ns, N, ns, ot, ns, 1, ql, N, 1, Y, ld, 1, EpiStore());
+  }
+  __syncthreads();
+  EpiFresh<T> epi{x.G(s), ld, &dmax};
+  cta_gemm<T>(N, N, ns, qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
+  if constexpr (!std::is_same<T, double>::value) {
+    if (c.dg64 == 2 && record) {
+      // the refreshed G itself against G_FP64 (the path-precision copies of
+      // Q_R and Q_L are no longer needed: Y64 takes their space)
+      __syncthreads();
+      double* y64 = reinterpret_cast<double*>(x.QRt());
+      cta_gemm<double>(ns, N, ns, Xinv, ns, 1, QL, N, 1, y64, N, 1, EpiStore());
+      __syncthreads();
+      double g_s = 0.0;
+      EpiDiff64<T> ed{x.G(s), ld, &dmax64, &g_s};
+      cta_gemm<double>(N, N, ns, QR, 1, N, y64, N, 1, (double*)nullptr, 0, 0, ed);
+    }
+  }
+  __syncthreads();
+}
 
 // G <- 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T at stabilisation point b; records
 // max |G - G_fresh| when record != 0, and the weight's log|det| and sign.
@@ -1426,8 +1498,7 @@ template <typename T>
 __device__ void refresh(Cta<T>& x, int b, bool record) {
   const ChainDesc& c = x.c;
   Smem<T>& sh = x.sh;
-  const int N = c.N, ld = c.ld;
-  T* Y = x.Yb();
+  const int N = c.N;
   T dmax = T(0);
   double dmax64 = 0.0;
   double sign_total = 1.0;
@@ -1443,55 +1514,7 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
   gj_invert2(x, n, O, la, sg);
   x.mark(kPhLU);
   for (int s = 0; s < x.nspec(); ++s) {
-    // Y = X Q_L^T (n x N), G_fresh = 1 - Q_R Y, in the path precision
-    const T* qr = reinterpret_cast<const T*>(QR[s]);
-    const T* ql = reinterpret_cast<const T*>(QL[s]);
-    if constexpr (!std::is_same<T, double>::value) {
-      if (c.dg64 == 1 && record) {
-        // Y64 = O^{-1} Q_L^T (n x N, FP64, in the space of the path-precision
-        // copies of Q_R and Q_L, which are written after it), then
-        // max |G - (1 - Q_R Y64)| over the propagated G
-        double* y64 = reinterpret_cast<double*>(x.QRt());
-        cta_gemm<double>(n[s], N, n[s], O[s], n[s], 1, QL[s], N, 1, y64, N, 1, EpiStore());
-        __syncthreads();
-        EpiDiff64<T> ed{x.G(s), ld, &dmax64};
-        cta_gemm<double>(N, N, n[s], QR[s], 1, N, y64, N, 1, (double*)nullptr, 0, 0, ed);
-        __syncthreads();
-      }
-      T* qrt = x.QRt();
-      T* qlt = x.QLt();
-      PQMC_FOR_2D(k, 0, n[s], i, 0, N) {
-        qrt[(long)k * N + i] = (T)QR[s][(long)k * N + i];
-        qlt[(long)k * N + i] = (T)QL[s][(long)k * N + i];
-      }
-      qr = qrt;
-      ql = qlt;
-      __syncthreads();
-    }
-    if constexpr (std::is_same<T, double>::value) {
-      cta_gemm<T>(n[s], N, n[s], O[s], n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
-    } else {
-      // O^{-1} to the path precision once, then a path-precision product
-      T* ot = x.Ot();
-      for (int e = threadIdx.x; e < n[s] * n[s]; e += blockDim.x) ot[e] = (T)O[s][e];
-      __syncthreads();
-      cta_gemm<T>(n[s], N, n[s], ot, n[s], 1, ql, N, 1, Y, ld, 1, EpiStore());
-    }
-    __syncthreads();
-    EpiFresh<T> epi{x.G(s), ld, &dmax};
-    cta_gemm<T>(N, N, n[s], qr, 1, N, Y, ld, 1, (T*)nullptr, 0, 0, epi);
-    if constexpr (!std::is_same<T, double>::value) {
-      if (c.dg64 == 2 && record) {
-        // the refreshed G itself against G_FP64 (the path-precision copies of
-        // Q_R and Q_L are no longer needed: Y64 takes their space)
-        __syncthreads();
-        double* y64 = reinterpret_cast<double*>(x.QRt());
-        cta_gemm<double>(n[s], N, n[s], O[s], n[s], 1, QL[s], N, 1, y64, N, 1, EpiStore());
-        __syncthreads();
-        EpiDiff64<T> ed{x.G(s), ld, &dmax64};
-        cta_gemm<double>(N, N, n[s], QR[s], 1, N, y64, N, 1, (double*)nullptr, 0, 0, ed);
-      }
-    }
+    assemble_spin(x, s, QR[s], QL[s], O[s], n[s], record, dmax, dmax64);
     const double l_tot = c.Rlog[(b * 2 + s) * 2 + 0] + la[s] + c.Llog[(b * 2 + s) * 2 + 0];
     const double s_tot = c.Rlog[(b * 2 + s) * 2 + 1] * sg[s] * c.Llog[(b * 2 + s) * 2 + 1];
     if (threadIdx.x == 0) {
@@ -1501,14 +1524,13 @@ __device__ void refresh(Cta<T>& x, int b, bool record) {
     sign_total *= s_tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0)
+  x.mark(kPhAssemble);
+  const double dm = cta_max((c.dg64 && record) ? dmax64 : (double)dmax, sh.red);
+  if (threadIdx.x == 0) {
     for (int s = x.nspec(); s < 2; ++s) {
       sh.logw_spin[s] = 0.0;
       sh.sign_spin[s] = 1.0;
     }
-  x.mark(kPhAssemble);
-  const double dm = cta_max((c.dg64 && record) ? dmax64 : (double)dmax, sh.red);
-  if (threadIdx.x == 0) {
     const double dmax = dm;
     if (!isfinite(dmax)) sh.err |= kErrNaN;
     if (record) {

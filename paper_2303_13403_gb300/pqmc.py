@@ -274,10 +274,10 @@ class Context:
         return out[: n.value]
 
     PHASES = ("flip", "flush", "wrap", "stack", "qr", "refresh", "measure", "total", "qr_form", "overlap", "lu",
-              "assemble", "gj_pivot", "gj_elim", "gj_tail")
+              "assemble", "gj_pivot", "gj_elim", "gj_tail", "flush_vec")
 
     def phase_cycles(self, chain=0):
-        out = (C.c_longlong * 15)()
+        out = (C.c_longlong * 16)()
         _check(load().pqmc_get_phase_cycles(self._h, chain, out), self._h)
         return dict(zip(self.PHASES, list(out)))
 
