@@ -40,8 +40,8 @@
  * keeps no reference after the call returns.
  *
  * Errors: every entry point returns a pqmc_status; nothing is thrown across
- * the ABI and the library never aborts. After PQMC_ESTAB or PQMC_ENAN the
- * context keeps the error (sticky) and refuses further sweeps and
+ * the ABI and the library never aborts. After PQMC_ESTAB, PQMC_ENAN or
+ * PQMC_ETIMEOUT the context keeps the error (sticky) and refuses further sweeps and
  * checkpoints until pqmc_restore loads a good checkpoint; pqmc_last_error()
  * gives a one-line reason. Entry points that read results synchronise the
  * context's stream first.
@@ -63,8 +63,9 @@ typedef enum {
     PQMC_ECUDA = 3,     /* a CUDA call failed (launch, copy, no device) */
     PQMC_ESTAB = 4,     /* singular matrix in the stabilisation (zero pivot / zero column) */
     PQMC_ENAN = 5,      /* NaN or Inf in a ratio or in G */
-    PQMC_ETIMEOUT = 6   /* reserved, never returned: the kernels wait on nothing but
-                           their own CTA barriers, so no device-side wait can time out */
+    PQMC_ETIMEOUT = 6   /* a bounded device-side wait gave up: the only such wait is the
+                           BF16X3 path's wait for its tensor-core products (chains kept in
+                           global memory on 512-thread CTAs); every other wait is a CTA barrier */
 } pqmc_status;
 
 /* Arithmetic of the wrap and delayed-update products. The stabilisation
@@ -73,9 +74,10 @@ typedef enum {
 typedef enum {
     PQMC_FP64 = 0,      /* everything FP64 */
     PQMC_FP32 = 1,      /* G, ratios, wrap and updates in FP32 */
-    PQMC_BF16X3 = 2     /* G and ratios FP32; wrap and update products as
-                           three BF16 tensor-core products (hi*hi + hi*lo + lo*hi),
-                           FP32 accumulation */
+    PQMC_BF16X3 = 2     /* G and ratios FP32; the wrap products as three BF16
+                           tensor-core products (hi*hi + hi*lo + lo*hi), FP32
+                           accumulation (tcgen05 for chains kept in global memory);
+                           the rank-k delayed updates in FP32 */
 } pqmc_precision;
 
 typedef enum { PQMC_HONEYCOMB = 0, PQMC_SQUARE = 1, PQMC_HONEYCOMB_TV = 2 } pqmc_lattice_kind;
@@ -258,8 +260,8 @@ pqmc_status pqmc_checkpoint(pqmc_ctx* ctx, void* buf, size_t* len);
  * accept_log (cta_threads and dense_chains may differ: they do not change the
  * results). Later sweeps then continue the checkpointed run exactly: the same
  * Philox draws, accept decisions, G and records. Clears a sticky
- * PQMC_ESTAB / PQMC_ENAN of the context, so a failed run can resume from
- * its last good checkpoint. PQMC_EINVAL (nothing loaded) when
+ * PQMC_ESTAB / PQMC_ENAN / PQMC_ETIMEOUT of the context, so a failed run
+ * can resume from its last good checkpoint. PQMC_EINVAL (nothing loaded) when
  * the data is not a checkpoint of this library or was taken from a context
  * that differs in any of the above. Synchronises. */
 pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len);
@@ -374,6 +376,18 @@ pqmc_status pqmc_get_launch(pqmc_ctx* ctx, int* out);
  * frees a small device buffer; synchronises the device.  PQMC_ECUDA on a
  * CUDA failure. */
 pqmc_status pqmc_probe_pipes(double* out);
+
+/* Test hook of the tensor-core split-BF16 product the BF16X3 path uses for
+ * chains kept in global memory (no counterpart in the paper): one CTA
+ * computes C = A B with A and B split into BF16 hi + lo parts and the three
+ * products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 by tcgen05
+ * MMAs in tensor memory.  Device pointers: A is M x K row-major (trans_a = 0)
+ * or K x M row-major holding A^T (trans_a != 0), B is K x N row-major, C is
+ * M x N row-major (written).  1 <= M, N, K <= 4096.  Runs on `stream`
+ * (NULL: the legacy default stream) and synchronises it.  PQMC_ETIMEOUT when
+ * the bounded wait for the tensor cores' completion gave up. */
+pqmc_status pqmc_test_tc_gemm(int M, int N, int K, const float* d_A, int trans_a, const float* d_B, float* d_C,
+                              void* stream);
 
 /* Error bar of the sign-reweighted estimator <s O>/<s> of the Method
  * section, as pqmc_measure computes it: the records are split into n_groups

@@ -193,8 +193,10 @@ pqmc_status sync_check(pqmc_ctx* ctx) {
   e = cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "error word copy");
   if (herr) {
-    ctx->sticky = (herr & kErrNaN) ? PQMC_ENAN : PQMC_ESTAB;
-    ctx->err = (herr & kErrNaN) ? "NaN or Inf in a ratio or in G" : "singular matrix in the stabilisation";
+    ctx->sticky = (herr & kErrNaN) ? PQMC_ENAN : (herr & kErrStab) ? PQMC_ESTAB : PQMC_ETIMEOUT;
+    ctx->err = (herr & kErrNaN) ? "NaN or Inf in a ratio or in G"
+               : (herr & kErrStab) ? "singular matrix in the stabilisation"
+                                   : "the bounded wait for the tensor cores' completion gave up";
     return (pqmc_status)ctx->sticky;
   }
   return PQMC_OK;

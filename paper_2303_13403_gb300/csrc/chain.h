@@ -22,7 +22,7 @@ enum : int {
 };
 
 // error bits written by the kernels
-enum : int { kErrNaN = 1, kErrStab = 2 };
+enum : int { kErrNaN = 1, kErrStab = 2, kErrTimeout = 4 };
 
 // Mutable per-chain counters, in device memory.
 struct ChainState {

@@ -18,10 +18,14 @@ int ctas_per_sm(int prec, int tpb, int boost) {
   return (256 / tpb) * (prec == 0 ? 1 : 2) * (boost ? 2 : 1);
 }
 
+// BF16X3 launches of 512-thread CTAs reserve the tensor-core staging area
+int tc_launch(int prec, int tpb) { return (prec == 2 && tpb == 512) ? 1 : 0; }
+
 // Largest resident footprint a launch offers per chain.
 size_t smem_resident_cap(int prec, int tpb, int boost) {
   const size_t per_sm = 233472, reserve = 1024;
-  const size_t per_cta = per_sm / ctas_per_sm(prec, tpb, boost) - reserve;
+  size_t per_cta = per_sm / ctas_per_sm(prec, tpb, boost) - reserve;
+  if (tc_launch(prec, tpb)) per_cta -= kTcBytes + 128;
   const size_t fixed = smem_fixed(prec);
   return per_cta > fixed ? per_cta - fixed : 0;
 }
@@ -44,16 +48,31 @@ cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains,
 }
 
 cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res) {
-  if (prec == 0) return prepare_sweep_f64(tpb, res);
-  if (boost) return prepare_sweep_f32_dense(tpb, res);
-  return prepare_sweep_f32(tpb, res);
+  if (prec == 0) return prepare_sweep_f64(tpb, res, 0);
+  if (boost) return prepare_sweep_f32_dense(tpb, res, 0);
+  return prepare_sweep_f32(tpb, res, tc_launch(prec, tpb));
 }
 
 cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains, int n, uint64_t seed,
                          uint32_t* sweep_ctr, int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {
-  if (prec == 0) return launch_sweep_f64(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
-  if (boost) return launch_sweep_f32_dense(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
-  return launch_sweep_f32(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);
+  if (prec == 0) return launch_sweep_f64(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream, 0);
+  if (boost)
+    return launch_sweep_f32_dense(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream, 0);
+  return launch_sweep_f32(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream,
+                          tc_launch(prec, tpb));
+}
+
+// --------------------------------------------------------------------------
+// Test kernel of the tensor-core split-BF16 GEMM (pqmc_test_tc_gemm).
+
+__global__ void __launch_bounds__(512, 1) tc_gemm_test_kernel(int M, int N, int K, const float* A, int trans_a,
+                                                             const float* B, float* C, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* st = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const uint32_t tmem = tc_alloc(st);
+  if (trans_a) cta_gemm_tc(M, N, K, A, 1, M, B, N, 1, C, N, 1, EpiStore(), st, tmem, err, kErrTimeout);
+  else cta_gemm_tc(M, N, K, A, K, 1, B, N, 1, C, N, 1, EpiStore(), st, tmem, err, kErrTimeout);
+  tc_free(tmem);
 }
 
 // --------------------------------------------------------------------------
@@ -250,6 +269,40 @@ extern "C" pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_sta
   if (herr) {
     set_init_error((herr & kErrNaN) ? "pqmc_green_noalloc: NaN or Inf in G" : "pqmc_green_noalloc: singular matrix");
     return (herr & kErrNaN) ? PQMC_ENAN : PQMC_ESTAB;
+  }
+  return PQMC_OK;
+}
+
+extern "C" pqmc_status pqmc_test_tc_gemm(int M, int N, int K, const float* d_A, int trans_a, const float* d_B,
+                                         float* d_C, void* stream) {
+  using namespace pqmc;
+  if (M < 1 || N < 1 || K < 1 || M > 4096 || N > 4096 || K > 4096 || !d_A || !d_B || !d_C) {
+    set_init_error("pqmc_test_tc_gemm: bad sizes or NULL pointer");
+    return PQMC_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* d_err = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_err, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  const int smem = (int)(kTcBytes + 128);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_gemm_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) {
+    tc_gemm_test_kernel<<<1, 512, smem, st>>>(M, N, K, d_A, trans_a, d_B, d_C, d_err);
+    e = cudaGetLastError();
+  }
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (d_err) cudaFreeAsync(d_err, st);
+  cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_init_error(std::string("pqmc_test_tc_gemm: ") + cudaGetErrorString(e));
+    return PQMC_ECUDA;
+  }
+  if (herr & kErrTimeout) {
+    set_init_error("pqmc_test_tc_gemm: tensor-core completion wait gave up");
+    return PQMC_ETIMEOUT;
   }
   return PQMC_OK;
 }

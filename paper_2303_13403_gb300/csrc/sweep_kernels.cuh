@@ -42,6 +42,7 @@
 #include "chain.h"
 #include "model.h"
 #include "philox.cuh"
+#include "tc_gemm.cuh"
 
 namespace pqmc {
 
@@ -288,20 +289,6 @@ __device__ void cta_gemm_bf16x3(int M, int Nn, int K, const float* A, int sai, i
   }
 }
 
-// Path GEMM of the wrap and of the delayed update: split-precision tensor
-// cores when the chain runs the BF16X3 path, CUDA-core FMA otherwise.
-template <typename T, typename Epi>
-__device__ void path_gemm(const ChainDesc& c, int M, int Nn, int K, const T* A, int sai, int sak, const T* B, int sbk,
-                          int sbj, T* C, int sci, int scj, Epi epi) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (c.tc) {
-      cta_gemm_bf16x3(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
-      return;
-    }
-  }
-  cta_gemm<T>(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
-}
-
 // --------------------------------------------------------------------------
 // shared memory of one chain CTA
 
@@ -357,6 +344,8 @@ struct Cta {
   ScratchLayout L;
   bool resident;
   FlipBuf<T>* fb;
+  unsigned char* tcs = nullptr;     // tensor-core staging area (BF16X3, chains in global memory), or null
+  uint32_t tmem = 0;                // its TMEM accumulator
   __device__ T* G(int s) const { return Gp + (long)s * c.N * c.ld; }
   __device__ T* Gt() const { return reinterpret_cast<T*>(scr + L.gt); }
   __device__ T* Ub() const { return reinterpret_cast<T*>(scr + L.u); }
@@ -416,6 +405,32 @@ struct Cta {
     }
   }
 };
+
+// Path GEMM of the wrap (deep = true, K = N) and of the delayed update
+// (deep = false, K = accepted flips of a block).  On the BF16X3 path the
+// wrap runs as split-precision tensor-core products: tcgen05 MMAs into tensor
+// memory when the CTA holds a staging area for them (a chain kept in global
+// memory on a 512-thread CTA), mma.sync otherwise.  The delayed update is a
+// rank-a correction (a <= 64) whose cost is reading and writing G: it runs
+// in FP32 on the CUDA cores on the BF16X3 path too (measured faster than
+// either tensor-core form at 162-648 sites, and exact to FP32).  FP32 and
+// FP64 paths: CUDA-core FMA.
+template <typename T, typename Epi>
+__device__ void path_gemm(Cta<T>& x, bool deep, int M, int Nn, int K, const T* A, int sai, int sak, const T* B,
+                          int sbk, int sbj, T* C, int sci, int scj, Epi epi) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (x.c.tc && deep) {
+      if (x.tcs) {
+        cta_gemm_tc(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi, x.tcs, x.tmem, &x.sh.err, kErrTimeout);
+        __syncthreads();
+      } else {
+        cta_gemm_bf16x3(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
+      }
+      return;
+    }
+  }
+  cta_gemm<T>(M, Nn, K, A, sai, sak, B, sbk, sbj, C, sci, scj, epi);
+}
 
 // --------------------------------------------------------------------------
 // Metropolis updates of one slice with delayed updates in blocks of kBlock
@@ -526,7 +541,7 @@ __device__ void flush_block(Cta<T>& x, int a, bool pivot) {
     __syncthreads();
     cta_gemm<T>(a, N, a, &fb.Tu[s][0][0], kBlock + 1, 1, Wbuf, ld, 1, MW, ld, 1, EpiStore());
     __syncthreads();
-    path_gemm<T>(c, N, N, a, Ubuf, 1, N, MW, ld, 1, Gs, ld, 1, EpiSub());
+    path_gemm<T>(x, false, N, N, a, Ubuf, 1, N, MW, ld, 1, Gs, ld, 1, EpiSub());
     __syncthreads();
   }
   x.mark(kPhFlush);
@@ -587,7 +602,8 @@ __device__ void apply_vectors(Cta<T>& x, int a) {
   const int N = c.N, ld = c.ld;
   T* Us[2] = {reinterpret_cast<T*>(x.scr + x.L.u), reinterpret_cast<T*>(x.scr + x.L.u2)};
   T* Vs[2] = {reinterpret_cast<T*>(x.scr + x.L.w), reinterpret_cast<T*>(x.scr + x.L.mw)};
-  for (int sp = 0; sp < 2; ++sp) path_gemm<T>(c, N, N, a, Us[sp], 1, N, Vs[sp], ld, 1, x.G(sp), ld, 1, EpiSub());
+  for (int sp = 0; sp < 2; ++sp)
+    path_gemm<T>(x, false, N, N, a, Us[sp], 1, N, Vs[sp], ld, 1, x.G(sp), ld, 1, EpiSub());
   __syncthreads();
   x.mark(kPhFlush);
 }
@@ -853,17 +869,17 @@ __device__ void wrap(Cta<T>& x, int tau, int dir) {
     if (gz) return;
     // Gt = e^{-dtau K} G, G = Gt e^{+dtau K}
     for (int s = 0; s < x.nspec(); ++s) {
-      path_gemm<T>(c, N, N, N, Em, 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
+      path_gemm<T>(x, true, N, N, N, Em, 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
       __syncthreads();
-      path_gemm<T>(c, N, N, N, Gt, ld, 1, Ep, ld, 1, x.G(s), ld, 1, EpiStore());
+      path_gemm<T>(x, true, N, N, N, Gt, ld, 1, Ep, ld, 1, x.G(s), ld, 1, EpiStore());
       __syncthreads();
     }
   } else {
     if (!gz) {
       for (int s = 0; s < x.nspec(); ++s) {
-        path_gemm<T>(c, N, N, N, Ep, 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
+        path_gemm<T>(x, true, N, N, N, Ep, 1, ld, x.G(s), ld, 1, Gt, ld, 1, EpiStore());
         __syncthreads();
-        path_gemm<T>(c, N, N, N, Gt, ld, 1, Em, ld, 1, x.G(s), ld, 1, EpiStore());
+        path_gemm<T>(x, true, N, N, N, Gt, ld, 1, Em, ld, 1, x.G(s), ld, 1, EpiStore());
         __syncthreads();
       }
     }
@@ -1792,13 +1808,24 @@ __global__ void __launch_bounds__(TPB, MINB) init_kernel(const ChainDesc* chains
 template <typename T, int TPB, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) sweep_kernel(const ChainDesc* chains, uint64_t seed,
                                                        const uint32_t* sweep_ctr, int n_sweeps, int do_measure,
-                                                       size_t res_bytes, int* err) {
+                                                       size_t res_bytes, int* err, int tc_on) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (chains[blockIdx.x].st->err) return;
   const uint32_t sweep0 = *sweep_ctr;
   Cta<T> x = make_cta<T>(chains[blockIdx.x], smem_raw, res_bytes, seed);
   Smem<T>& sh = x.sh;
   load_state(x);
+  if constexpr (std::is_same<T, float>::value && TPB == 512) {
+    // BF16X3 chains kept in global memory run their products on the tensor
+    // cores: a staging area after the dynamic shared memory the launch
+    // reserves for it, and TMEM columns held until the CTA ends
+    if (tc_on && x.c.tc && !x.resident) {
+      const size_t fbb = flipbuf_bytes((int)sizeof(T));
+      const uintptr_t at = reinterpret_cast<uintptr_t>(smem_raw) + al16(sizeof(Smem<T>)) + (res_bytes > fbb ? res_bytes : fbb);
+      x.tcs = reinterpret_cast<unsigned char*>((at + 127) & ~(uintptr_t)127);
+      x.tmem = tc_alloc(x.tcs);
+    }
+  }
   const long long t_start = clock64();
   for (int k = 0; k < n_sweeps; ++k) {
     const uint32_t sw = sweep0 + (uint32_t)k;
@@ -1808,6 +1835,9 @@ __global__ void __launch_bounds__(TPB, MINB) sweep_kernel(const ChainDesc* chain
     if (sh.err) break;
   }
   if (threadIdx.x == 0) sh.cyc[kPhTotal] += clock64() - t_start;
+  if constexpr (std::is_same<T, float>::value && TPB == 512) {
+    if (x.tcs) tc_free(x.tmem);
+  }
   write_back(x);
   store_state(x, err);
 }
@@ -1834,17 +1864,24 @@ static cudaError_t launch_init_t(const ChainDesc* d_chains, int chain0, int n, u
 // Advances the device-side sweep index after a sweep launch (sweep.cu).
 cudaError_t launch_advance(uint32_t* sweep_ctr, int n, cudaStream_t stream);
 
+// tc_on: the launch reserves the tensor-core staging area (BF16X3 on
+// 512-thread CTAs)
 template <typename T, int TPB, int MINB>
-static cudaError_t prepare_sweep_t(size_t res) {
+static size_t sweep_smem(size_t res, int tc_on) {
+  return dyn_smem<T>(res) + ((std::is_same<T, float>::value && TPB == 512 && tc_on) ? kTcBytes + 128 : 0);
+}
+
+template <typename T, int TPB, int MINB>
+static cudaError_t prepare_sweep_t(size_t res, int tc_on) {
   return cudaFuncSetAttribute(sweep_kernel<T, TPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)dyn_smem<T>(res));
+                              (int)sweep_smem<T, TPB, MINB>(res, tc_on));
 }
 
 template <typename T, int TPB, int MINB>
 static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr, int n_sweeps,
-                                  int measure, size_t res, int* d_err, cudaStream_t stream) {
-  sweep_kernel<T, TPB, MINB><<<n, TPB, dyn_smem<T>(res), stream>>>(d_chains, seed, sweep_ctr, n_sweeps, measure, res,
-                                                                   d_err);
+                                  int measure, size_t res, int* d_err, cudaStream_t stream, int tc_on) {
+  sweep_kernel<T, TPB, MINB><<<n, TPB, sweep_smem<T, TPB, MINB>(res, tc_on), stream>>>(
+      d_chains, seed, sweep_ctr, n_sweeps, measure, res, d_err, tc_on);
   const cudaError_t e = cudaGetLastError();
   return e != cudaSuccess ? e : launch_advance(sweep_ctr, n_sweeps, stream);
 }
@@ -1856,19 +1893,19 @@ static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t see
                               int* d_err, cudaStream_t stream, int b_at) {                                         \
     PQMC_TPB_DISPATCH(launch_init_t, d_chains, chain0, n, seed, res, d_err, stream, b_at);                          \
   }                                                                                                                \
-  cudaError_t prepare_sweep_##P(int tpb, size_t res) { PQMC_TPB_DISPATCH(prepare_sweep_t, res); }                  \
+  cudaError_t prepare_sweep_##P(int tpb, size_t res, int tc_on) { PQMC_TPB_DISPATCH(prepare_sweep_t, res, tc_on); } \
   cudaError_t launch_sweep_##P(int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,      \
-                               int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream) {           \
-    PQMC_TPB_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream);         \
+                               int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream, int tc_on) { \
+    PQMC_TPB_DISPATCH(launch_sweep_t, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream, tc_on);  \
   }
 
 // Per-path launchers (one translation unit each).
 #define PQMC_DECLARE_LAUNCHERS(P)                                                                                 \
   cudaError_t launch_init_##P(int tpb, const ChainDesc* d_chains, int chain0, int n, uint64_t seed, size_t res,    \
                               int* d_err, cudaStream_t stream, int b_at);                                          \
-  cudaError_t prepare_sweep_##P(int tpb, size_t res);                                                              \
+  cudaError_t prepare_sweep_##P(int tpb, size_t res, int tc_on);                                                  \
   cudaError_t launch_sweep_##P(int tpb, const ChainDesc* d_chains, int n, uint64_t seed, uint32_t* sweep_ctr,      \
-                               int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
+                               int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream, int tc_on);
 PQMC_DECLARE_LAUNCHERS(f64)
 PQMC_DECLARE_LAUNCHERS(f32)
 PQMC_DECLARE_LAUNCHERS(f32_dense)

@@ -107,6 +107,8 @@ SIGNATURES = [
     ("pqmc_autotune", C.c_int, [C.c_int, C.POINTER(ChainSpec), C.POINTER(Opts), C.POINTER(Tune)]),
     ("pqmc_get_launch", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("pqmc_probe_pipes", C.c_int, [C.POINTER(C.c_double)]),
+    ("pqmc_test_tc_gemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
 ]
 
 
@@ -344,6 +346,12 @@ def probe_pipes():
     out = (C.c_double * 12)()
     _check(load().pqmc_probe_pipes(out))
     return dict(zip(PROBE_KEYS, list(out)))
+
+
+def test_tc_gemm(M, N, K, d_A, trans_a, d_B, d_C, stream=None):
+    """pqmc_test_tc_gemm: device pointers (ints); C = A B by the tensor-core split-BF16 product."""
+    _check(load().pqmc_test_tc_gemm(M, N, K, C.c_void_p(d_A), 1 if trans_a else 0, C.c_void_p(d_B),
+                                    C.c_void_p(d_C), C.c_void_p(stream) if stream else None))
 
 
 def host_jackknife(sO, s):

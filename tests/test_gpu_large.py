@@ -1,7 +1,8 @@
 """Oracle parity where the large configurations run (GPU, through the C-ABI).
 
 Chains of 162, 288 and 648 sites keep G in global memory; the reduced paths
-run them on 512-thread CTAs.  After each whole sweep the GPU's G is compared,
+run them on 512-thread CTAs, the BF16X3 path with its products on the
+tensor cores (tcgen05).  After each whole sweep the GPU's G is compared,
 element by element, with the oracle's definition of the equal-time Green's
 function (Method section: G = 1 - B_R (B_L B_R)^{-1} B_L, products
 re-orthonormalised after every slice) on the GPU's own final fields: FP64 to
@@ -43,6 +44,8 @@ CASES = [
     (9, 4.0, pqmc.FP32, 2, 2),
     (12, 4.0, pqmc.FP32, 2, 2),
     (18, 2.0, pqmc.FP32, 2, 1),
+    (9, 4.0, pqmc.BF16X3, 2, 2),
+    (12, 4.0, pqmc.BF16X3, 2, 1),
 ]
 
 
@@ -66,8 +69,10 @@ def test_sweeps_against_green_definition(L, two_theta, prec, n_stab, sweeps):
                 err = np.abs(G - Gd).max() / np.abs(Gd).max()
                 assert err < 1e-10, (N, k, s, err)
             else:
+                # FP32: the benchmark spec's bound; BF16X3 (about 16 significant
+                # bits in its products): an order of magnitude above it
                 err = np.abs(G - Gd).max()
-                assert err < 1e-4, (N, k, s, err)
+                assert err < (1e-4 if prec == pqmc.FP32 else 2e-3), (N, k, s, err)
         # the trace invariant of the projector: Tr(1 - G_sigma) = N_sigma
         assert abs(N - np.trace(ctx.green(0, 0)) - N // 2) < (1e-9 if prec == pqmc.FP64 else 1e-3)
     rec = ctx.measurements(0)
