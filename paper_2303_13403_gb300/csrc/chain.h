@@ -105,7 +105,7 @@ namespace pqmc {
 //             (kw x ld, T) of each spin (u, w for spin 0; u2, mw for
 //             spin 1), kw = max(delayed block, kBlock); for t-V blocks A_S
 //             (u), W and M W (w, mw); and the per-block flip buffers
-//   stack   : M64 (N x n, FP64, column-major), then a region holding the two
+//   stack   : M64 (N x n, FP64, column-major, ld m64_ld(N)), then a region holding the two
 //             path-precision product buffers Mt, Mt2 (N x n, T, row-major)
 //             and later the FP64 Q of the QR; Householder betas / R_jj;
 //             the Gram matrix and pivots of the Cholesky QR
@@ -129,6 +129,11 @@ PQMC_HDI constexpr size_t flipbuf_bytes(int tsize) {
 
 // kd: the delayed-update block of the chain (its update vectors are sized
 // for max(kd, kBlock) flips)
+// leading dimension of the stack phase's FP64 block M in the scratch: odd, so
+// that the Gram matrix's threads, each on its own columns, read different
+// shared-memory banks
+PQMC_HDI constexpr int m64_ld(int N) { return N | 1; }
+
 PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize, int kd) {
   ScratchLayout L;
   const size_t Nn = (size_t)N * n;
@@ -142,7 +147,7 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize, int kd) {
   L.fb = L.mw + al16(kw * ld * tsize);
   size_t flush = L.fb + flipbuf_bytes(tsize);
   L.m64 = 0;
-  L.mtq = al16(Nn * 8);
+  L.mtq = al16((size_t)m64_ld(N) * n * 8);
   L.mt2 = L.mtq + al16(Nn * tsize);
   const size_t two_mt = 2 * al16(Nn * tsize);
   const size_t mtq_sz = two_mt > al16(Nn * 8) ? two_mt : al16(Nn * 8);

@@ -922,14 +922,15 @@ __device__ void log_det_of(Cta<T>& x, const double* d, int n, int extra_sign_fli
   __syncthreads();
 }
 
-// Householder QR of the column-major N x n matrix M (ld N).  The explicit
+// Householder QR of the column-major N x n matrix M (ld ldm).  The explicit
 // orthonormal factor goes to Q (column-major, ld N); log|det R| and sign(det R)
 // are returned to every thread.  Each reflector is applied to all trailing
 // columns in three CTA-wide phases (partial column dots over row chunks, one
 // thread per column adds the chunks, a parallel rank-1 update), so no FP64
 // work sits in warp-shuffle reductions.
 template <typename T>
-__device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta, double* A, int c0, int c1, int j) {
+__device__ void householder_apply(Cta<T>& x, int N, int lda, const double* v, double beta, double* A, int c0, int c1,
+                                  int j) {
   double* part = x.qpart();
   double* w = x.qw();
   if (c1 <= c0) return;
@@ -937,7 +938,7 @@ __device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta
   {
     const int p = threadIdx.x & (kQRParts - 1);
     for (int col = c0 + (int)(threadIdx.x / kQRParts); col < c1; col += (int)(blockDim.x / kQRParts)) {
-      const double* a = A + (long)col * N;
+      const double* a = A + (long)col * lda;
       double d0 = 0.0, d1 = 0.0;
       int i = j + p;
       for (; i + kQRParts < N; i += 2 * kQRParts) {
@@ -965,7 +966,7 @@ __device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta
     const int rows = N - j, total = rows * (c1 - c0);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int cl = e / rows, i = j + (e - cl * rows), col = c0 + cl;
-      A[(long)col * N + i] = fma(-v[i], w[col], A[(long)col * N + i]);
+      A[(long)col * lda + i] = fma(-v[i], w[col], A[(long)col * lda + i]);
     }
   }
   __syncthreads();
@@ -973,10 +974,10 @@ __device__ void householder_apply(Cta<T>& x, int N, const double* v, double beta
 
 // reflector of column j (warp 0): v = x - alpha e_j stored over the column
 template <typename T>
-__device__ void householder_reflector(Cta<T>& x, int N, double* M, int j) {
+__device__ void householder_reflector(Cta<T>& x, int N, int ldm, double* M, int j) {
   const int lane = threadIdx.x & 31;
   if ((threadIdx.x >> 5) == 0) {
-    double* v = M + (long)j * N;
+    double* v = M + (long)j * ldm;
     double s = 0.0;
     for (int i = j + lane; i < N; i += 32) s = fma(v[i], v[i], s);
     s = warp_sum(s);
@@ -995,22 +996,23 @@ __device__ void householder_reflector(Cta<T>& x, int N, double* M, int j) {
 }
 
 template <typename T>
-__device__ void qr_householder(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs, double& sgn) {
+__device__ void qr_householder(Cta<T>& x, int N, int ldm, int n, double* M, double* Q, double& logabs, double& sgn) {
   for (int j = 0; j < n; ++j) {
-    householder_reflector(x, N, M, j);
-    householder_apply(x, N, M + (long)j * N, x.qbeta()[j], M, j + 1, n, j);
+    householder_reflector(x, N, ldm, M, j);
+    householder_apply(x, N, ldm, M + (long)j * ldm, x.qbeta()[j], M, j + 1, n, j);
   }
   x.mark(kPhQR);
   PQMC_FOR_2D(col, 0, n, i, 0, N) Q[(long)col * N + i] = (i == col) ? 1.0 : 0.0;
   __syncthreads();
-  for (int j = n - 1; j >= 0; --j) householder_apply(x, N, M + (long)j * N, x.qbeta()[j], Q, j, n, j);
+  for (int j = n - 1; j >= 0; --j) householder_apply(x, N, N, M + (long)j * ldm, x.qbeta()[j], Q, j, n, j);
   log_det_of(x, x.qalpha(), n, 0, logabs, sgn);
   x.mark(kPhQRForm);
 }
 
 // Upper triangle (2 x 2 tiles on or above the diagonal) of C = M^T M for the
-// column-major N x n matrix M (ld N); C row-major n x n.
-static __device__ void gram_upper_f64(int n, int N, const double* M, double* C) {
+// column-major N x n matrix M (ld ldm, odd so that the threads' columns fall
+// in different shared-memory banks); C row-major n x n.
+static __device__ void gram_upper_f64(int n, int N, int ldm, const double* M, double* C) {
   // 2 x 2 output tiles (ti, tj), ti <= tj, enumerated over a flat index so
   // that every warp carries only tiles of the upper triangle (the FP64 pipe
   // takes the same time for a partial warp as for a full one)
@@ -1020,10 +1022,10 @@ static __device__ void gram_upper_f64(int n, int N, const double* M, double* C) 
     while (tj >= tn - ti) { tj -= tn - ti; ++ti; }
     tj += ti;
     const int i0 = ti << 1, j0 = tj << 1;
-    const double* a0 = M + (long)i0 * N;
-    const double* a1 = M + (long)min(i0 + 1, n - 1) * N;
-    const double* b0 = M + (long)j0 * N;
-    const double* b1 = M + (long)min(j0 + 1, n - 1) * N;
+    const double* a0 = M + (long)i0 * ldm;
+    const double* a1 = M + (long)min(i0 + 1, n - 1) * ldm;
+    const double* b0 = M + (long)j0 * ldm;
+    const double* b1 = M + (long)min(j0 + 1, n - 1) * ldm;
     double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
 #pragma unroll 4
     for (int k = 0; k < N; ++k) {
@@ -1054,14 +1056,14 @@ static __device__ void gram_upper_f64(int n, int N, const double* M, double* C) 
 // 1e6); the caller then takes the Householder QR.  R has a positive diagonal,
 // so only log|det R| = (1/2) sum_k log(pivot_k) is returned.
 template <typename T>
-__device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, double& logabs) {
+__device__ bool qr_cholesky(Cta<T>& x, int N, int ldm, int n, double* M, double* Q, double& logabs) {
   Smem<T>& sh = x.sh;
   double* C = x.chol();                 // n x n row-major (upper part): Gram, then Schur complements
   double* U = C + (long)n * n;          // n x n row-major (upper part): U_kj = R_kj / R_kk
   double* d0 = U + (long)n * n;         // original diagonal
   double* ip = d0 + n;                  // 1 / pivot
   double* isq = ip + n;                 // 1 / sqrt(pivot)
-  gram_upper_f64(n, N, M, C);
+  gram_upper_f64(n, N, ldm, M, C);
   if (threadIdx.x == 0) sh.chol_bad = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) d0[k] = C[(long)k * n + k];
@@ -1115,7 +1117,7 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
       for (int i = threadIdx.x; i < N; i += blockDim.x) {
         double mv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) mv[u] = u < kb ? M[(long)(K + u) * N + i] : 0.0;
+        for (int u = 0; u < 4; ++u) mv[u] = u < kb ? M[(long)(K + u) * ldm + i] : 0.0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (u < kb) {
@@ -1127,7 +1129,7 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u < kb) M[(long)(K + u) * N + i] = mv[u];
+          if (u < kb) M[(long)(K + u) * ldm + i] = mv[u];
       }
       __syncthreads();
       const int j0 = K + kb;
@@ -1136,11 +1138,11 @@ __device__ bool qr_cholesky(Cta<T>& x, int N, int n, double* M, double* Q, doubl
         const int t0 = (int)threadIdx.x / N, r0 = (int)threadIdx.x - t0 * N;
         int jj = j0 + t0, i = r0;
         while (jj < n) {
-          double acc = M[(long)jj * N + i];
+          double acc = M[(long)jj * ldm + i];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (u < kb) acc = fma(-M[(long)(K + u) * N + i], U[(long)(K + u) * n + jj], acc);
-          M[(long)jj * N + i] = acc;
+            if (u < kb) acc = fma(-M[(long)(K + u) * ldm + i], U[(long)(K + u) * n + jj], acc);
+          M[(long)jj * ldm + i] = acc;
           i += sr;
           jj += sq;
           if (i >= N) { i -= N; ++jj; }
@@ -1315,6 +1317,7 @@ template <typename T>
 __device__ void push_R(Cta<T>& x, int b) {
   const ChainDesc& c = x.c;
   const int N = c.N, n_stab = c.n_stab;
+  const int ldm = m64_ld(N);
   double* M = x.M64();
   for (int s = 0; s < x.nspec(); ++s) {
     const int n = x.nsig(s);
@@ -1324,7 +1327,7 @@ __device__ void push_R(Cta<T>& x, int b) {
     double prev_l = 0.0, prev_s = 1.0;
     if (b == 0) {
       x.stage(0);
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = x.vexp(0, s, i) * P[(long)k * N + i];
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * ldm + i] = x.vexp(0, s, i) * P[(long)k * N + i];
       __syncthreads();
     } else {
       const double* prev = stack_block(x, c.Rst, b - 1, s);
@@ -1339,13 +1342,13 @@ __device__ void push_R(Cta<T>& x, int b) {
         __syncthreads();
         T* t = Mt; Mt = Mt2; Mt2 = t;
       }
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * ldm + i] = (double)Mt[(long)i * n + k];
       __syncthreads();
     }
     double la, sg = 1.0;
     x.mark(kPhStack);
-    if (std::is_same<T, double>::value || !qr_cholesky(x, N, n, M, x.Q64(), la))
-      qr_householder(x, N, n, M, x.Q64(), la, sg);
+    if (std::is_same<T, double>::value || !qr_cholesky(x, N, ldm, n, M, x.Q64(), la))
+      qr_householder(x, N, ldm, n, M, x.Q64(), la, sg);
     copy_block(x.Q64(), stack_block(x, c.Rst, b, s), N * n);
     x.mark(kPhQR);
     if (threadIdx.x == 0) {
@@ -1362,6 +1365,7 @@ template <typename T>
 __device__ void push_L(Cta<T>& x, int b) {
   const ChainDesc& c = x.c;
   const int N = c.N, n_stab = c.n_stab;
+  const int ldm = m64_ld(N);
   double* M = x.M64();
   for (int s = 0; s < x.nspec(); ++s) {
     const int n = x.nsig(s);
@@ -1371,7 +1375,7 @@ __device__ void push_L(Cta<T>& x, int b) {
     double prev_l = 0.0, prev_s = 1.0;
     if (b == c.nb) {
       x.stage(c.Ltau + 1);
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = x.vexp(c.Ltau + 1, s, i) * P[(long)k * N + i];
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * ldm + i] = x.vexp(c.Ltau + 1, s, i) * P[(long)k * N + i];
       __syncthreads();
     } else {
       const double* prev = stack_block(x, c.Lst, b + 1, s);
@@ -1385,13 +1389,13 @@ __device__ void push_L(Cta<T>& x, int b) {
         PQMC_FOR_2D(i, 0, N, k, 0, n) Mt[(long)i * n + k] = x.vexpT(tau, s, i) * Mt2[(long)i * n + k];
         __syncthreads();
       }
-      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * N + i] = (double)Mt[(long)i * n + k];
+      PQMC_FOR_2D(k, 0, n, i, 0, N) M[(long)k * ldm + i] = (double)Mt[(long)i * n + k];
       __syncthreads();
     }
     double la, sg = 1.0;
     x.mark(kPhStack);
-    if (std::is_same<T, double>::value || !qr_cholesky(x, N, n, M, x.Q64(), la))
-      qr_householder(x, N, n, M, x.Q64(), la, sg);
+    if (std::is_same<T, double>::value || !qr_cholesky(x, N, ldm, n, M, x.Q64(), la))
+      qr_householder(x, N, ldm, n, M, x.Q64(), la, sg);
     copy_block(x.Q64(), stack_block(x, c.Lst, b, s), N * n);
     x.mark(kPhQR);
     if (threadIdx.x == 0) {

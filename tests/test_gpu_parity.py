@@ -176,6 +176,26 @@ def test_fp32_stabilisation_error_distribution():
     assert np.percentile(errs, 99.9) <= 1e-4 and errs.max() < 1e-2
 
 
+def test_fp32_error_against_fp64_relative_to_g():
+    """Against G_FP64 (assembled in FP64 from the FP64 factors), FP32 at a
+    2-slice interval: after the first sweep, the 99.9th percentile of
+    max |G - G_FP64| stays below 1e-4, and every stabilisation's error
+    relative to max(1, max |G_FP64|) stays below 1e-4 (the absolute tail
+    belongs to configurations whose G has entries of size 30-70, where FP32
+    storage alone carries ~4e-6)."""
+    spec = workloads.GUTZ_72[8.0]
+    out = {}
+    for mode in (1, 3):
+        ctx = pqmc.Context([spec] * 32, prec=pqmc.FP32, seed=3, n_stab=2, dg_fp64=mode)
+        ctx.sweep(5)
+        out[mode] = np.concatenate([ctx.stab_errors(c)[41:] for c in range(32)])
+        ctx.close()
+    assert len(out[1]) == len(out[3]) == 32 * 4 * 41
+    assert np.percentile(out[1], 99.9) <= 1e-4 and out[1].max() < 1e-2
+    assert out[3].max() <= 1e-4
+    assert np.all(out[3] <= out[1] + 1e-30)
+
+
 @pytest.mark.parametrize("prec", [pqmc.FP64, pqmc.FP32, pqmc.BF16X3])
 def test_mc_energy_within_3sigma_of_exact(prec):
     """64 independent chains on the 8-site cluster; the pooled estimates of E,
