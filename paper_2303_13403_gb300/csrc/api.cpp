@@ -71,7 +71,8 @@ struct pqmc_ctx {
   std::vector<unsigned char> host_arena;   // initial contents of the device arena
   unsigned char* d_arena = nullptr;
   size_t arena_bytes = 0;
-  ChainDesc* d_desc = nullptr;
+  ChainDesc* d_desc = nullptr;            // descriptors by chain index (initialisation launches)
+  ChainDesc* d_desc_run = nullptr;        // the same in sweep-launch order: costliest chains first
   int* d_err = nullptr;
   size_t off_last = 0;                     // n_chains x kRecord latest records
   size_t res_bytes = 0;                    // shared memory offered for resident chains
@@ -200,6 +201,28 @@ pqmc_status sync_check(pqmc_ctx* ctx) {
     return (pqmc_status)ctx->sticky;
   }
   return PQMC_OK;
+}
+
+// The sweep launch runs one CTA per chain; a batch of uneven chains starts
+// its costliest chains first (longest-processing-time order, cost
+// N^3 (Ltau + 2), ties in chain order), so that the long chains are not left
+// for the tail of the launch.  Each CTA reads its chain's own descriptor, so
+// the order changes no result.
+cudaError_t upload_run_order(pqmc_ctx* ctx) {
+  const int n = (int)ctx->chains.size();
+  std::vector<int> order(n);
+  for (int c = 0; c < n; ++c) order[c] = c;
+  auto cost = [&](int c) {
+    const HostChain& h = ctx->chains[c];
+    return (double)h.N * h.N * h.N * (h.Ltau + 2);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::vector<ChainDesc> run(n);
+  for (int i = 0; i < n; ++i) run[i] = ctx->desc[order[i]];
+  cudaError_t e = cudaMemcpyAsync(ctx->d_desc_run, run.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);   // run is a local buffer
+  return e;
 }
 
 pqmc_status autotune_cached(int n, const pqmc_chain_spec* specs, const pqmc_opts& o, pqmc_tune* out);
@@ -404,6 +427,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   e = cudaMalloc(&ctx->d_arena, ctx->arena_bytes);
   if (e != cudaSuccess) { pqmc_free(ctx); return fail(nullptr, PQMC_ENOMEM, std::string("device arena: ") + cudaGetErrorString(e)); }
   e = cudaMalloc(&ctx->d_desc, sizeof(ChainDesc) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_desc_run, sizeof(ChainDesc) * n);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 2 * sizeof(int));
   if (e == cudaSuccess) ctx->d_sweep = reinterpret_cast<uint32_t*>(ctx->d_err + 1);
   if (e != cudaSuccess) { pqmc_free(ctx); return fail(nullptr, PQMC_ENOMEM, "device descriptors"); }
@@ -458,6 +482,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   e = cudaMemcpyAsync(ctx->d_arena, A.data(), ctx->arena_bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = upload_run_order(ctx);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int), ctx->stream);
   if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->res_bytes);
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
@@ -494,6 +519,7 @@ pqmc_status retarget(pqmc_ctx* ctx, int kd, int tpb) {
   for (auto& d : ctx->desc) d.kb = kd;
   cudaError_t e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * ctx->desc.size(),
                                   cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = upload_run_order(ctx);
   if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->res_bytes);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
@@ -507,11 +533,11 @@ double time_sweeps(pqmc_ctx* ctx) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NAN;
   const int n = (int)ctx->chains.size();
-  cudaError_t e = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, n, ctx->opts.seed, ctx->d_sweep, 1, 0,
+  cudaError_t e = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc_run, n, ctx->opts.seed, ctx->d_sweep, 1, 0,
                                ctx->res_bytes, ctx->d_err, ctx->stream);
   if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k)
-    e = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, n, ctx->opts.seed, ctx->d_sweep, 1, 0,
+    e = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc_run, n, ctx->opts.seed, ctx->d_sweep, 1, 0,
                      ctx->res_bytes, ctx->d_err, ctx->stream);
   if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -860,7 +886,7 @@ pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      const cudaError_t el = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, (int)ctx->chains.size(), ctx->opts.seed,
+      const cudaError_t el = launch_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc_run, (int)ctx->chains.size(), ctx->opts.seed,
                                           ctx->d_sweep, n_sweeps, meas, ctx->res_bytes, ctx->d_err, ctx->stream);
       e = cudaStreamEndCapture(ctx->stream, &graph);
       if (e == cudaSuccess) e = el;
@@ -1224,6 +1250,7 @@ void pqmc_free(pqmc_ctx* ctx) {
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   if (ctx->d_desc) cudaFree(ctx->d_desc);
+  if (ctx->d_desc_run) cudaFree(ctx->d_desc_run);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

@@ -227,7 +227,7 @@ __device__ void cta_gemm(int M, int Nn, int K, const TA* A, int sai, int sak, co
 // with every operand split as x = hi + lo, hi = bf16(x), lo = bf16(x - hi),
 // and C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 by
 // mma.sync.m16n8k16 (Henry, Tang & Heinecke 2019 use the same split).  Each
-// warp owns 16 x 8 output tiles; operands are read with arbitrary strides
+// warp owns 16 x 32 output tiles; operands are read with arbitrary strides
 // (zero outside the matrix) and split on the fly.
 
 static __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
@@ -250,41 +250,59 @@ static __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4],
 template <typename Epi>
 __device__ void cta_gemm_bf16x3(int M, int Nn, int K, const float* A, int sai, int sak, const float* B, int sbk,
                                 int sbj, float* C, int sci, int scj, Epi epi) {
+  // each warp owns a 16 x 32 output tile: the A fragment of a k-step is
+  // loaded and split once and used by the four 16 x 8 products of the tile
+  constexpr int kNs = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int g = lane >> 2, tg = lane & 3;
-  const int tm = (M + 15) >> 4, tn = (Nn + 7) >> 3;
+  const int tm = (M + 15) >> 4, tn = (Nn + 8 * kNs - 1) / (8 * kNs);
   auto a_at = [&](int r, int k) -> float { return (r < M && k < K) ? A[(long)r * sai + (long)k * sak] : 0.0f; };
   auto b_at = [&](int k, int n) -> float { return (k < K && n < Nn) ? B[(long)k * sbk + (long)n * sbj] : 0.0f; };
   for (int t = warp; t < tm * tn; t += nw) {
-    const int m0 = (t / tn) << 4, n0 = (t % tn) << 3;
-    const int r0 = m0 + g, r1 = m0 + g + 8, nn = n0 + g;
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const int m0 = (t / tn) << 4, n0 = (t % tn) * 8 * kNs;
+    const int r0 = m0 + g, r1 = m0 + g + 8;
+    const int nsub = min(kNs, (Nn - n0 + 7) >> 3);          // sub-tiles holding columns (warp-uniform)
+    float c[kNs][4];
+#pragma unroll
+    for (int q = 0; q < kNs; ++q) c[q][0] = c[q][1] = c[q][2] = c[q][3] = 0.f;
     for (int k0 = 0; k0 < K; k0 += 16) {
       const int k = k0 + 2 * tg;
       const float av[8] = {a_at(r0, k), a_at(r0, k + 1), a_at(r1, k), a_at(r1, k + 1),
                            a_at(r0, k + 8), a_at(r0, k + 9), a_at(r1, k + 8), a_at(r1, k + 9)};
-      const float bv[4] = {b_at(k, nn), b_at(k + 1, nn), b_at(k + 8, nn), b_at(k + 9, nn)};
-      __nv_bfloat16 ah[8], al[8], bh[4], bl[4];
+      __nv_bfloat16 ah[8], al[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) split_bf16(av[q], ah[q], al[q]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) split_bf16(bv[q], bh[q], bl[q]);
       const uint32_t AH[4] = {pack2(ah[0], ah[1]), pack2(ah[2], ah[3]), pack2(ah[4], ah[5]), pack2(ah[6], ah[7])};
       const uint32_t AL[4] = {pack2(al[0], al[1]), pack2(al[2], al[3]), pack2(al[4], al[5]), pack2(al[6], al[7])};
-      const uint32_t BH[2] = {pack2(bh[0], bh[1]), pack2(bh[2], bh[3])};
-      const uint32_t BL[2] = {pack2(bl[0], bl[1]), pack2(bl[2], bl[3])};
-      mma_bf16(c, AH, BL);
-      mma_bf16(c, AL, BH);
-      mma_bf16(c, AH, BH);
+#pragma unroll
+      for (int q = 0; q < kNs; ++q) {
+        if (q < nsub) {
+          const int nn = n0 + 8 * q + g;
+          const float bv[4] = {b_at(k, nn), b_at(k + 1, nn), b_at(k + 8, nn), b_at(k + 9, nn)};
+          __nv_bfloat16 bh[4], bl[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) split_bf16(bv[u], bh[u], bl[u]);
+          const uint32_t BH[2] = {pack2(bh[0], bh[1]), pack2(bh[2], bh[3])};
+          const uint32_t BL[2] = {pack2(bl[0], bl[1]), pack2(bl[2], bl[3])};
+          mma_bf16(c[q], AH, BL);
+          mma_bf16(c[q], AL, BH);
+          mma_bf16(c[q], AH, BH);
+        }
+      }
     }
-    const int cc = n0 + 2 * tg;
-    if (r0 < M) {
-      if (cc < Nn) epi(C, sci, scj, r0, cc, c[0]);
-      if (cc + 1 < Nn) epi(C, sci, scj, r0, cc + 1, c[1]);
-    }
-    if (r1 < M) {
-      if (cc < Nn) epi(C, sci, scj, r1, cc, c[2]);
-      if (cc + 1 < Nn) epi(C, sci, scj, r1, cc + 1, c[3]);
+#pragma unroll
+    for (int q = 0; q < kNs; ++q) {
+      if (q < nsub) {
+        const int cc = n0 + 8 * q + 2 * tg;
+        if (r0 < M) {
+          if (cc < Nn) epi(C, sci, scj, r0, cc, c[q][0]);
+          if (cc + 1 < Nn) epi(C, sci, scj, r0, cc + 1, c[q][1]);
+        }
+        if (r1 < M) {
+          if (cc < Nn) epi(C, sci, scj, r1, cc, c[q][2]);
+          if (cc + 1 < Nn) epi(C, sci, scj, r1, cc + 1, c[q][3]);
+        }
+      }
     }
   }
 }

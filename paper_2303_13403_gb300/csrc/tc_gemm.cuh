@@ -158,19 +158,48 @@ __device__ void cta_gemm_tc(int M, int Nn, int K, const float* A, int sai, int s
         // split the A slice (128 x kw) and the B slice (kw x nt, stored as
         // its transpose, nt x kw) into the hi / lo tiles (zero outside the
         // operands); consecutive threads walk the operand's unit-stride index
-        for (int e = tid; e < kTcM * kw; e += nthr) {
-          int r, k;
-          if (sai == 1) { r = e % kTcM; k = e / kTcM; } else { k = e % kw; r = e / kw; }
-          const int i = m0 + r, kk = k0 + k;
-          const float v = (i < M && kk < K) ? A[(long)i * sai + (long)kk * sak] : 0.0f;
-          tc_split_store(ahi, alo, tc_off(r, k), v);
+        // (the loads of a batch of eight elements are issued before its
+        // stores, so that eight loads per thread are in flight at once)
+        constexpr int kB = 8;
+        for (int e0 = tid; e0 < kTcM * kw; e0 += kB * nthr) {
+          float v[kB];
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            const int e = e0 + q * nthr;
+            int r, k;
+            if (sai == 1) { r = e % kTcM; k = e / kTcM; } else { k = e % kw; r = e / kw; }
+            const int i = m0 + r, kk = k0 + k;
+            v[q] = (e < kTcM * kw && i < M && kk < K) ? A[(long)i * sai + (long)kk * sak] : 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            const int e = e0 + q * nthr;
+            if (e < kTcM * kw) {
+              int r, k;
+              if (sai == 1) { r = e % kTcM; k = e / kTcM; } else { k = e % kw; r = e / kw; }
+              tc_split_store(ahi, alo, tc_off(r, k), v[q]);
+            }
+          }
         }
-        for (int e = tid; e < nt * kw; e += nthr) {
-          int n, k;
-          if (sbj == 1) { n = e % nt; k = e / nt; } else { k = e % kw; n = e / kw; }
-          const int j = n0 + n, kk = k0 + k;
-          const float v = (j < Nn && kk < K) ? B[(long)kk * sbk + (long)j * sbj] : 0.0f;
-          tc_split_store(bhi, blo, tc_off(n, k), v);
+        for (int e0 = tid; e0 < nt * kw; e0 += kB * nthr) {
+          float v[kB];
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            const int e = e0 + q * nthr;
+            int n, k;
+            if (sbj == 1) { n = e % nt; k = e / nt; } else { k = e % kw; n = e / kw; }
+            const int j = n0 + n, kk = k0 + k;
+            v[q] = (e < nt * kw && j < Nn && kk < K) ? B[(long)kk * sbk + (long)j * sbj] : 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < kB; ++q) {
+            const int e = e0 + q * nthr;
+            if (e < nt * kw) {
+              int n, k;
+              if (sbj == 1) { n = e % nt; k = e / nt; } else { k = e % kw; n = e / kw; }
+              tc_split_store(bhi, blo, tc_off(n, k), v[q]);
+            }
+          }
         }
         // the tiles written by the threads (generic proxy) are read by the
         // tensor cores (async proxy)
