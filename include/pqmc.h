@@ -157,6 +157,17 @@ typedef struct {
                                max(1, max |G_FP64|) per spin (the error relative to the size of
                                G). Costs two extra FP64 products per stabilisation; changes
                                nothing else (same decisions, same G) */
+    int spread;             /* nonzero: sweep the chains with grid-wide kernels instead of one CTA
+                               per chain, for a few large chains (one chain uses every SM): per
+                               block of 32 sites a one-CTA decision kernel and a tiled update of
+                               G, the wrap as tiled products, the stabilisation as tiled FP64
+                               products with a blocked Cholesky QR and a blocked Gauss-Jordan
+                               inverse.  Same precisions, decisions and Philox stream as the
+                               one-CTA path (results agree to rounding).  Needs at most 32
+                               Hubbard chains sharing N, N_sigma and Ltau; delay_k is ignored
+                               (blocks of 32 sites); no dg_fp64.  PQMC_ESTAB when a stack
+                               block's Cholesky factor breaks down (cond above about 1e6: use a
+                               shorter n_stab) */
 } pqmc_opts;
 
 /* Sign-reweighted estimates <s O>/<s> with jackknife errors over bins of
@@ -372,7 +383,11 @@ pqmc_status pqmc_get_launch(pqmc_ctx* ctx, int* out);
  * out[3..5] clock cycles of one dependent FP64 FMA, add + divide, and
  * add + square root, out[6..9] clock cycles per FP64 warp instruction of one
  * warp with 1, 8, 16 and 32 active lanes (8 independent chains per lane),
- * out[10] SM count, out[11] the reported SM clock in MHz.  Allocates and
+ * out[10] SM count, out[11] the reported SM clock in MHz, out[12] FP64
+ * TFLOP/s of a launch whose warps alternate between the FMA and the
+ * tensor-core loop, out[13] its time over the mean of the two pure launches
+ * (1: the two share one pipe; 0.5: they run side by side); out must hold 14
+ * doubles.  Allocates and
  * frees a small device buffer; synchronises the device.  PQMC_ECUDA on a
  * CUDA failure. */
 pqmc_status pqmc_probe_pipes(double* out);

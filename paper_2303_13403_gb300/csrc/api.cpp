@@ -26,6 +26,7 @@
 #include "chain.h"
 #include "model.h"
 #include "philox.cuh"
+#include "spread.h"
 
 namespace pqmc {
 size_t smem_resident_cap(int prec, int tpb, int boost);
@@ -33,6 +34,7 @@ int ctas_per_sm(int prec, int tpb, int boost);
 cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains, int chain0, int n, uint64_t seed,
                         size_t res, int* d_err, cudaStream_t stream, int b_at);
 cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res);
+cudaError_t launch_advance(uint32_t* sweep_ctr, int n, cudaStream_t stream);
 cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains, int n, uint64_t seed,
                          uint32_t* sweep_ctr, int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream);
 }  // namespace pqmc
@@ -55,7 +57,7 @@ struct HostChain {
   int N, ld, nup, ndn, nmax, Ltau, nb, nfld;
   size_t off_fields, off_G, off_Rst, off_Lst, off_Rlog, off_Llog, off_meas, off_dG,
       off_acc, off_state, off_P, off_scratch, off_expKm, off_expKp, off_expKm64, off_K64, off_eps, off_bonds,
-      off_sbonds;
+      off_sbonds, off_spread;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -77,8 +79,11 @@ struct pqmc_ctx {
   size_t off_last = 0;                     // n_chains x kRecord latest records
   size_t res_bytes = 0;                    // shared memory offered for resident chains
   uint32_t* d_sweep = nullptr;             // sweep index read by the sweep kernel
-  struct GraphEntry { int n_sweeps, measure; cudaGraphExec_t exec; };
-  std::vector<GraphEntry> graphs;          // captured (sweep, advance) pairs
+  struct GraphEntry { int n_sweeps, measure; cudaGraphExec_t exec; size_t kernels; };
+  std::vector<GraphEntry> graphs;          // captured (sweep, advance) pairs; spread: one sweep of
+                                           // each direction (n_sweeps = parity)
+  bool spread = false;                     // chains swept by grid-wide kernel sequences
+  SpreadPlan plan;
   int tpb = 256;                           // threads per chain CTA
   int scratch_kd = kBlock;                 // delayed block the per-chain scratch is sized for
   int boost = 0;                           // 1: reduced-path kernels built for twice the CTAs per SM
@@ -249,6 +254,21 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     return fail(nullptr, PQMC_EINVAL, "cta_threads 512 is built for the reduced paths only");
   if (o.dense_chains && o.prec != PQMC_FP64 && o.cta_threads == 256)
     return fail(nullptr, PQMC_EINVAL, "dense_chains needs cta_threads 64 or 128");
+  if (o.spread) {
+    // chains swept by grid-wide kernels: one shape, Hubbard chains, blocks of
+    // kBlock sites, no FP64 diagnostic
+    if (n * 2 > 64) return fail(nullptr, PQMC_EINVAL, "spread: at most 32 chains");
+    if (o.dense_chains || o.dg_fp64) return fail(nullptr, PQMC_EINVAL, "spread: no dense_chains or dg_fp64");
+    for (int c = 0; c < n; ++c) {
+      const pqmc_chain_spec& a = specs[c];
+      const pqmc_chain_spec& z = specs[0];
+      if (is_tv(a)) return fail(nullptr, PQMC_EINVAL, "spread: Hubbard chains only");
+      if (n_sites(a.lattice) != n_sites(z.lattice) || a.trial.N_up != z.trial.N_up || a.trial.N_dn != z.trial.N_dn ||
+          std::lround(a.two_theta / a.dtau) != std::lround(z.two_theta / z.dtau))
+        return fail(nullptr, PQMC_EINVAL, "spread: chains must share N, N_sigma and Ltau");
+    }
+    o.delay_k = kBlock;
+  }
   for (int c = 0; c < n; ++c) {
     std::string why;
     if (check_spec(specs[c], o.n_stab, why) != PQMC_OK) return fail(nullptr, PQMC_EINVAL, "chain " + std::to_string(c) + ": " + why);
@@ -349,6 +369,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     h.off_dG = take((size_t)kDGHistory * 8);
     h.off_acc = take((size_t)std::max(o.accept_log, 1));
     h.off_state = take(sizeof(ChainState));
+    h.off_spread = o.spread ? take(spread_layout(h.N, h.ld, h.nmax, (int)ctx->tsize).total) : 0;
   }
   ctx->off_last = take((size_t)n * kRecord * 8);
   // default CTA size (measured on GB300): the FP64 path packs 4 chains of 64
@@ -359,7 +380,7 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   int nmax_sites = 0;
   for (const HostChain& h : ctx->chains) nmax_sites = std::max(nmax_sites, h.N);
   const int reduced_tpb = (nmax_sites >= 128 && !o.dense_chains) ? 512 : 256;
-  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? 64 : reduced_tpb);
+  ctx->tpb = o.cta_threads != 0 ? o.cta_threads : (ctx->prec == PQMC_FP64 ? (o.spread ? 256 : 64) : reduced_tpb);
   {
     ctx->boost = (ctx->prec != PQMC_FP64 && o.dense_chains) ? 1 : 0;
     const size_t cap = smem_resident_cap(ctx->prec, ctx->tpb, ctx->boost);
@@ -478,6 +499,24 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     d.acc_log = reinterpret_cast<uint8_t*>(b + h.off_acc);
     d.acc_cap = o.accept_log;
     d.st = reinterpret_cast<ChainState*>(b + h.off_state);
+    d.spread = o.spread ? b + h.off_spread : nullptr;
+  }
+  if (o.spread) {
+    SpreadPlan& P = ctx->plan;
+    const HostChain& h0 = ctx->chains[0];
+    P.prec = ctx->prec;
+    P.n = n;
+    P.N = h0.N; P.ld = h0.ld; P.nup = h0.nup; P.ndn = h0.ndn; P.nmax = h0.nmax;
+    P.Ltau = h0.Ltau; P.n_stab = o.n_stab; P.nb = h0.nb;
+    P.d_desc = ctx->d_desc;
+    P.seed = o.seed;
+    P.d_sweep = ctx->d_sweep;
+    P.d_err = ctx->d_err;
+    for (int c = 0; c < n; ++c) {
+      const ChainDesc& d = ctx->desc[c];
+      P.ch.push_back({d.spread, d.G, d.expKm, d.expKp, d.Rst, d.Lst});
+    }
+    ctx->spread = true;
   }
   e = cudaMemcpyAsync(ctx->d_arena, A.data(), ctx->arena_bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
@@ -870,14 +909,55 @@ pqmc_status pqmc_get_launch(pqmc_ctx* ctx, int* out) {
   return PQMC_OK;
 }
 
+namespace {
+
+// Sweeps of a spread context: one captured graph per (direction, measure)
+// holding the kernel sequence of one sweep and the advance of the sweep
+// index, replayed once per sweep in direction order.
+pqmc_status spread_sweeps(pqmc_ctx* ctx, int n_sweeps, int meas) {
+  for (int k = 0; k < n_sweeps; ++k) {
+    const int parity = (int)((ctx->sweep_index + (uint32_t)k) & 1u);
+    pqmc_ctx::GraphEntry* ge = nullptr;
+    for (auto& g : ctx->graphs)
+      if (g.n_sweeps == parity && g.measure == meas) ge = &g;
+    cudaError_t e = cudaSuccess;
+    if (!ge) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      size_t nodes = 0;
+      e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t el = spread_sweep(ctx->plan, parity, meas, ctx->stream);
+        if (el == cudaSuccess) el = launch_advance(ctx->d_sweep, 1, ctx->stream);
+        e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (e == cudaSuccess) e = el;
+      }
+      if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nullptr, &nodes);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "spread sweep graph capture");
+      ctx->graphs.push_back({parity, meas, exec, nodes});
+      ge = &ctx->graphs.back();
+    }
+    e = cudaGraphLaunch(ge->exec, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "spread sweep graph launch");
+    ctx->launches += (long)ge->kernels;
+  }
+  ctx->sweep_index += (uint32_t)n_sweeps;
+  return PQMC_OK;
+}
+
+}  // namespace
+
 pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
   NvtxRange range("pqmc_sweep");
   if (!ctx || n_sweeps < 0) return PQMC_EINVAL;
   if (ctx->sticky != PQMC_OK) return (pqmc_status)ctx->sticky;
   if (n_sweeps == 0) return PQMC_OK;
+  const int meas = measure ? 1 : 0;
+  if (ctx->spread) return spread_sweeps(ctx, n_sweeps, meas);
   // one captured graph per (n_sweeps, measure): the sweep launch and the
   // advance of the device-side sweep index, replayed on the context's stream
-  const int meas = measure ? 1 : 0;
   cudaGraphExec_t exec = nullptr;
   for (auto& g : ctx->graphs)
     if (g.n_sweeps == n_sweeps && g.measure == meas) exec = g.exec;
@@ -894,7 +974,7 @@ pqmc_status pqmc_sweep(pqmc_ctx* ctx, int n_sweeps, int measure) {
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep graph capture");
-    ctx->graphs.push_back({n_sweeps, meas, exec});
+    ctx->graphs.push_back({n_sweeps, meas, exec, 2});
   }
   e = cudaGraphLaunch(exec, ctx->stream);
   ctx->launches += 2;

@@ -83,6 +83,7 @@ struct ChainDesc {
   uint8_t* acc_log;        // accept bits
   long long acc_cap;
   ChainState* st;
+  unsigned char* spread;   // buffers of a chain swept by many CTAs (SpreadLayout), or null
 };
 static_assert(sizeof(ChainDesc) % sizeof(int) == 0, "descriptor copied word by word");
 
@@ -169,6 +170,65 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize, int kd) {
   L.ep = 2 * wrap;
   if (3 * wrap > t) L.em = L.ep = 0;
   L.total = (t + 255) & ~(size_t)255;
+  return L;
+}
+
+// Buffers of a chain whose sweep runs as a sequence of grid-wide kernels
+// (pqmc_opts.spread): byte offsets inside the chain's spread region, per
+// spin s.
+//   mt[s][0..1] : N x n (T, row-major, ld n) products advancing a stack block
+//   m64[s]      : N x n (FP64, column-major, ld N) block to factor
+//   c64[s]      : n x n (FP64, row-major) Gram matrix, then R in its upper part
+//   rinv[s]     : inverses of R's kSpPanel x kSpPanel diagonal blocks
+//   o64[s]      : n x n (FP64, row-major) Q_L^T Q_R, inverted in place
+//   tgj[s]      : kSpGJ x n block row saved by a Gauss-Jordan panel step
+//   pval, perm  : Gauss-Jordan pivots and row interchanges; d0 the Gram diagonal
+//   xt, qrt, qlt: path-precision copies of O^{-1} (n x n), Q_R and Q_L (N x n, ld N)
+//   y[s]        : n x ld (T) O^{-1} Q_L^T
+//   gt[s]       : N x ld (T) wrap intermediate
+//   u, w, mb    : U = E_S - G_{:,S} (N x kBlock, ld N), W = G_{S,:} (kBlock x ld) and
+//                 M (kBlock x kBlock) of the flips accepted in one block
+//   misc        : int na (accepted flips of the block), int bad[2] (Cholesky
+//                 breakdown), then 8-aligned: uint64 dmax (bits of max |G - G_fresh|),
+//                 double lchol[2] (log det R)
+constexpr int kSpPanel = 32;   // Cholesky panel width
+constexpr int kSpGJ = 16;      // Gauss-Jordan panel width
+struct SpreadLayout {
+  size_t mt[2][2], m64[2], c64[2], rinv[2], o64[2], tgj[2], pval[2], perm[2], d0[2], xt[2], qrt[2], qlt[2], y[2],
+      gt[2], u[2], w[2], mb[2], misc, total;
+};
+
+PQMC_HDI SpreadLayout spread_layout(int N, int ld, int n, int tsize) {
+  SpreadLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t Nn = (size_t)N * n, nn = (size_t)n * n, np = (size_t)((n + kSpPanel - 1) / kSpPanel);
+  for (int s = 0; s < 2; ++s) {
+    L.mt[s][0] = take(Nn * tsize);
+    L.mt[s][1] = take(Nn * tsize);
+    L.m64[s] = take(Nn * 8);
+    L.c64[s] = take(nn * 8);
+    L.rinv[s] = take(np * kSpPanel * kSpPanel * 8);
+    L.o64[s] = take(nn * 8);
+    L.tgj[s] = take((size_t)kSpGJ * n * 8);
+    L.pval[s] = take((size_t)n * 8);
+    L.perm[s] = take((size_t)n * 4);
+    L.d0[s] = take((size_t)n * 8);
+    L.xt[s] = take(nn * tsize);
+    L.qrt[s] = take(Nn * tsize);
+    L.qlt[s] = take(Nn * tsize);
+    L.y[s] = take((size_t)n * ld * tsize);
+    L.gt[s] = take((size_t)N * ld * tsize);
+    L.u[s] = take((size_t)N * kBlock * tsize);
+    L.w[s] = take((size_t)kBlock * ld * tsize);
+    L.mb[s] = take((size_t)kBlock * kBlock * tsize);
+  }
+  L.misc = take(64);
+  L.total = off;
   return L;
 }
 

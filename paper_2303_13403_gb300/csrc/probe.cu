@@ -61,6 +61,38 @@ __global__ void dmma_tput(double* sink, double a, double b) {
   if (s == 1.2345) sink[threadIdx.x] = s;
 }
 
+// even warps run the DFMA loop of dfma_tput, odd warps the DMMA loop of
+// dmma_tput: whether the two FP64 paths of an SM can be busy at the same time
+__global__ void dfma_dmma_mix(double* sink, double a, double b) {
+  const int warp = threadIdx.x >> 5;
+  double s = 0;
+  if ((warp & 1) == 0) {
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = threadIdx.x + c;
+    for (int i = 0; i < kIters; ++i)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+  } else {
+    double acc[4][2];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c][0] = acc[c][1] = 0.0;
+    const double av = a + threadIdx.x * 1e-9, bv = b - threadIdx.x * 1e-9;
+    for (int i = 0; i < kIters / 4; ++i) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                     : "+d"(acc[c][0]), "+d"(acc[c][1])
+                     : "d"(av), "d"(bv));
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s += acc[c][0] + acc[c][1];
+  }
+  if (s == 1.2345) sink[threadIdx.x] = s;
+}
+
 // one warp, `active` lanes running kChains independent FP64 chains: clock
 // cycles per FP64 warp instruction
 __global__ void dfma_partial(long long* cycles, double* sink, int active, double a, double b) {
@@ -144,6 +176,7 @@ extern "C" pqmc_status pqmc_probe_pipes(double* out) {
   const double ms_f = time_ms([&] { ffma_tput<<<blocks, threads>>>((float*)dsink, 0.999999f, 1e-7f); });
   const double ms_m = time_ms([&] { dmma_tput<<<blocks, threads>>>(dsink, 0.999999, 1e-7); });
   const double flop_mma = 2.0 * 8 * 8 * 4 * 4 * (kIters / 4) * (double)blocks * (threads / 32);
+  const double ms_x = time_ms([&] { dfma_dmma_mix<<<blocks, threads>>>(dsink, 0.999999, 1e-7); });
   long long cyc[8] = {0};
   const int lanes[4] = {1, 8, 16, 32};
   double per_instr[4];
@@ -169,5 +202,10 @@ extern "C" pqmc_status pqmc_probe_pipes(double* out) {
   for (int k = 0; k < 4; ++k) out[6 + k] = per_instr[k];   // cycles per FP64 warp instruction, 1/8/16/32 lanes
   out[10] = sms;
   out[11] = clk_khz / 1e3;                      // reported SM clock, MHz
+  // half the warps on each path: FP64 TFLOP/s of the mix, and its time
+  // against the two halves run one after the other (1: one shared pipe,
+  // 0.5: two independent ones)
+  out[12] = 0.5 * (flop_fma + flop_mma) / (ms_x * 1e-3) / 1e12;
+  out[13] = ms_x / (0.5 * (ms_d + ms_m));
   return PQMC_OK;
 }

@@ -1,0 +1,11 @@
+// Spread sweep (spread.cuh): the kernel sequence of the reduced paths (FP32
+// and split BF16; the FP64 stabilisation steps live in spread_f64.cu).
+#include "spread.cuh"
+
+namespace pqmc {
+
+cudaError_t spread_sweep_f32(const SpreadPlan& p, int parity, int measure, cudaStream_t st) {
+  return spread_sweep_t<float>(p, parity, measure, st);
+}
+
+}  // namespace pqmc

@@ -1,6 +1,7 @@
 // Host side of the sweep kernels: shared-memory budgets, the precision and
 // CTA-shape dispatch over the per-path translation units, the sweep-index
 // advance kernel, and the allocation-free single-chain initialisation.
+#include "spread.h"
 #include "sweep_kernels.cuh"
 
 namespace pqmc {
@@ -60,6 +61,13 @@ cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains
     return launch_sweep_f32_dense(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream, 0);
   return launch_sweep_f32(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream,
                           tc_launch(prec, tpb));
+}
+
+// chains swept by grid-wide kernel sequences (spread_f64.cu, spread_f32.cu)
+cudaError_t spread_sweep_f64(const SpreadPlan& p, int parity, int measure, cudaStream_t st);
+cudaError_t spread_sweep_f32(const SpreadPlan& p, int parity, int measure, cudaStream_t st);
+cudaError_t spread_sweep(const SpreadPlan& p, int parity, int measure, cudaStream_t st) {
+  return p.prec == PQMC_FP64 ? spread_sweep_f64(p, parity, measure, st) : spread_sweep_f32(p, parity, measure, st);
 }
 
 // --------------------------------------------------------------------------

@@ -479,14 +479,14 @@ __device__ __forceinline__ T uniform_of(uint64_t m53) {
 // place by one warp per species; Hubbard blocks need no pivoting (its pivots
 // are the accepted ratios), the bond blocks of the t-V model pivot on rows
 // (a single end of an accepted bond may have a vanishing ratio).
+// M = Gamma (1 + (1 - G_SS) Gamma)^{-1} of the a accepted flips of a block
+// into fb.Tu[s] for every species s (collective; G is the G of the block
+// start).
 template <typename T>
-__device__ void flush_block(Cta<T>& x, int a, bool pivot) {
-  const ChainDesc& c = x.c;
+__device__ void block_inverse(Cta<T>& x, int a, bool pivot) {
   FlipBuf<T>& fb = *x.fb;
-  const int N = c.N, ld = c.ld, ns = x.nspec();
+  const int ld = x.c.ld, ns = x.nspec();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* Ubuf = x.Ub();                                    // kBlock x N  (U column-major, ld N)
-  T* Wbuf = x.Wb();                                    // kBlock x ld (rows G_{S,:})
   PQMC_FOR_2D(sl, 0, ns * a, m, 0, a) {
     const int s = sl >= a ? 1 : 0, l = sl - s * a;
     const T g = x.G(s)[(long)fb.gsite[l] * ld + fb.gsite[m]];
@@ -546,6 +546,16 @@ __device__ void flush_block(Cta<T>& x, int a, bool pivot) {
       if (lane < a) X[l][lane] *= fb.cl[s][l];
   }
   __syncthreads();
+}
+
+template <typename T>
+__device__ void flush_block(Cta<T>& x, int a, bool pivot) {
+  const ChainDesc& c = x.c;
+  FlipBuf<T>& fb = *x.fb;
+  const int N = c.N, ld = c.ld, ns = x.nspec();
+  T* Ubuf = x.Ub();                                    // kBlock x N  (U column-major, ld N)
+  T* Wbuf = x.Wb();                                    // kBlock x ld (rows G_{S,:})
+  block_inverse(x, a, pivot);
   // per species: A_S = E_S - G_{:,S} (N x a, column-major) and W = G_{S,:}
   // (a x N) gathered before G changes, then MW = M W and G -= A_S MW
   T* MW = reinterpret_cast<T*>(x.scr + x.L.mw);
@@ -631,8 +641,13 @@ __device__ void apply_vectors(Cta<T>& x, int a) {
 // applied to G at once.  Within a delayed block a later sub-block reads its
 // diagonal block of G corrected by the update vectors of the flips already
 // accepted, G_SS - U_S V_S, so every decision sees the current G.
+// The proposals of one decision sub-block, sites i0 .. i0 + nbk - 1 of slice
+// tau (nbk <= kBlock), after a_done flips of the delayed block were accepted
+// (their update vectors in the scratch correct the diagonal block read from
+// G): warps 0 and 1 decide; sh.na receives the accepted count of the delayed
+// block, fb the accepted sites and their Delta, Delta / R.
 template <typename T>
-__device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
+__device__ void decide_sub_block(Cta<T>& x, int tau, uint32_t sweep, int i0, int nbk, int a_done) {
   const ChainDesc& c = x.c;
   Smem<T>& sh = x.sh;
   FlipBuf<T>& fb = *x.fb;
@@ -641,6 +656,87 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
   const int kap = x.gutz(tau) ? 1 : 0;
   int8_t* f = c.fields + (long)tau * c.nfld;
   const T dl[2][2] = {{(T)c.delta[kap][0][0], (T)c.delta[kap][0][1]}, {(T)c.delta[kap][1][0], (T)c.delta[kap][1][1]}};
+  if (warp < 2) {
+    // warp s (spin s): lane q holds column q of the spin's diagonal block in
+    // registers; the two warps exchange the spin ratios through shared
+    // memory once per proposal and take the same decision
+    const int s = warp;
+    T gs[kBlock];
+    const bool colq = lane < nbk;
+#pragma unroll
+    for (int r = 0; r < kBlock; ++r) gs[r] = (colq && r < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + lane] : T(0);
+    if (a_done > 0 && colq) {
+      // G_SS - U_S V_S over the vectors of the block's earlier flips
+      const T* U = reinterpret_cast<const T*>(x.scr + (s == 0 ? x.L.u : x.L.u2));
+      const T* V = reinterpret_cast<const T*>(x.scr + (s == 0 ? x.L.w : x.L.mw));
+      for (int l = 0; l < a_done; ++l) {
+        const T vq = V[(long)l * ld + i0 + lane];
+#pragma unroll
+        for (int r = 0; r < kBlock; ++r)
+          if (r < nbk) gs[r] = fma(-U[(long)l * N + i0 + r], vq, gs[r]);
+      }
+    }
+    // lane j: uniform (in the decision precision) and field of site i0 + j
+    T uj = T(2);
+    int flj = 1;
+    if (colq) {
+      const U4 w = philox4x32_10((uint32_t)(i0 + lane), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
+                                 (uint32_t)(x.seed >> 32));
+      uj = uniform_of<T>(((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11));
+      flj = (int)f[i0 + lane];
+    }
+    int a = a_done, bad = 0, nneg = 0;
+    const long long pos0 = sh.acc_pos;
+#pragma unroll
+    for (int j = 0; j < kBlock; ++j) {
+      if (j < nbk) {
+        const int si = __shfl_sync(0xffffffffu, flj, j) > 0 ? 0 : 1;
+        const T ds = dl[s][si];
+        const T rs = T(1) + ds * (T(1) - __shfl_sync(0xffffffffu, gs[j], j));
+        if (lane == 0) fb.rs[s][j] = rs;
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+        const T R = fb.rs[0][j] * fb.rs[1][j];
+        const bool acc = __shfl_sync(0xffffffffu, (int)(uj < (R < T(0) ? -R : R)), j) != 0;
+        if (s == 0 && lane == 0) {
+          if (!isfinite(R)) bad = 1;
+          if (pos0 + j < c.acc_cap) c.acc_log[pos0 + j] = acc ? 1 : 0;
+        }
+        if (acc) {
+          // G_rq += c G_rj G_jq for future rows r > j and columns q > j
+          const T y = lane > j ? (ds / rs) * gs[j] : T(0);
+#pragma unroll
+          for (int r = j + 1; r < kBlock; ++r) gs[r] = fma(__shfl_sync(0xffffffffu, gs[r], j), y, gs[r]);
+          if (lane == j) {
+            flj = -flj;
+            if (s == 0) f[i0 + j] = (int8_t)flj;
+          }
+          if (lane == 0) fb.fr[s][a] = ds / rs;
+          if (s == 0 && lane == 0) {
+            fb.gsite[a] = i0 + j;
+            fb.cl[0][a] = ds;
+            fb.cl[1][a] = dl[1][si];
+            nneg += R < T(0) ? 1 : 0;
+          }
+          ++a;
+        }
+      }
+    }
+    if (s == 0 && lane == 0) {
+      sh.na = a;
+      sh.acc_pos = pos0 + nbk;
+      sh.n_prop += nbk;
+      sh.n_acc += a - a_done;
+      if (nneg & 1) sh.sign_running = -sh.sign_running;
+      if (bad) sh.err |= kErrNaN;
+    }
+  }
+}
+
+template <typename T>
+__device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
+  const ChainDesc& c = x.c;
+  Smem<T>& sh = x.sh;
+  const int N = c.N;
   const int kd = c.kb;
   const int sub = kd < kBlock ? kd : kBlock;
 
@@ -649,80 +745,7 @@ __device__ void update_slice(Cta<T>& x, int tau, uint32_t sweep) {
     int a_done = 0;                                  // flips of the delayed block already accepted
     for (int i0 = d0; i0 < d1; i0 += sub) {
       const int nbk = min(sub, d1 - i0);
-      if (warp < 2) {
-        // warp s (spin s): lane q holds column q of the spin's diagonal block in
-        // registers; the two warps exchange the spin ratios through shared
-        // memory once per proposal and take the same decision
-        const int s = warp;
-        T gs[kBlock];
-        const bool colq = lane < nbk;
-#pragma unroll
-        for (int r = 0; r < kBlock; ++r) gs[r] = (colq && r < nbk) ? x.G(s)[(long)(i0 + r) * ld + i0 + lane] : T(0);
-        if (a_done > 0 && colq) {
-          // G_SS - U_S V_S over the vectors of the block's earlier flips
-          const T* U = reinterpret_cast<const T*>(x.scr + (s == 0 ? x.L.u : x.L.u2));
-          const T* V = reinterpret_cast<const T*>(x.scr + (s == 0 ? x.L.w : x.L.mw));
-          for (int l = 0; l < a_done; ++l) {
-            const T vq = V[(long)l * ld + i0 + lane];
-#pragma unroll
-            for (int r = 0; r < kBlock; ++r)
-              if (r < nbk) gs[r] = fma(-U[(long)l * N + i0 + r], vq, gs[r]);
-          }
-        }
-        // lane j: uniform (in the decision precision) and field of site i0 + j
-        T uj = T(2);
-        int flj = 1;
-        if (colq) {
-          const U4 w = philox4x32_10((uint32_t)(i0 + lane), (uint32_t)tau, sweep, c.chain_index, (uint32_t)x.seed,
-                                     (uint32_t)(x.seed >> 32));
-          uj = uniform_of<T>(((uint64_t)w.x0 << 21) | (uint64_t)(w.x1 >> 11));
-          flj = (int)f[i0 + lane];
-        }
-        int a = a_done, bad = 0, nneg = 0;
-        const long long pos0 = sh.acc_pos;
-#pragma unroll
-        for (int j = 0; j < kBlock; ++j) {
-          if (j < nbk) {
-            const int si = __shfl_sync(0xffffffffu, flj, j) > 0 ? 0 : 1;
-            const T ds = dl[s][si];
-            const T rs = T(1) + ds * (T(1) - __shfl_sync(0xffffffffu, gs[j], j));
-            if (lane == 0) fb.rs[s][j] = rs;
-            asm volatile("bar.sync 1, 64;" ::: "memory");
-            const T R = fb.rs[0][j] * fb.rs[1][j];
-            const bool acc = __shfl_sync(0xffffffffu, (int)(uj < (R < T(0) ? -R : R)), j) != 0;
-            if (s == 0 && lane == 0) {
-              if (!isfinite(R)) bad = 1;
-              if (pos0 + j < c.acc_cap) c.acc_log[pos0 + j] = acc ? 1 : 0;
-            }
-            if (acc) {
-              // G_rq += c G_rj G_jq for future rows r > j and columns q > j
-              const T y = lane > j ? (ds / rs) * gs[j] : T(0);
-#pragma unroll
-              for (int r = j + 1; r < kBlock; ++r) gs[r] = fma(__shfl_sync(0xffffffffu, gs[r], j), y, gs[r]);
-              if (lane == j) {
-                flj = -flj;
-                if (s == 0) f[i0 + j] = (int8_t)flj;
-              }
-              if (lane == 0) fb.fr[s][a] = ds / rs;
-              if (s == 0 && lane == 0) {
-                fb.gsite[a] = i0 + j;
-                fb.cl[0][a] = ds;
-                fb.cl[1][a] = dl[1][si];
-                nneg += R < T(0) ? 1 : 0;
-              }
-              ++a;
-            }
-          }
-        }
-        if (s == 0 && lane == 0) {
-          sh.na = a;
-          sh.acc_pos = pos0 + nbk;
-          sh.n_prop += nbk;
-          sh.n_acc += a - a_done;
-          if (nneg & 1) sh.sign_running = -sh.sign_running;
-          if (bad) sh.err |= kErrNaN;
-        }
-      }
+      decide_sub_block(x, tau, sweep, i0, nbk, a_done);
       __syncthreads();
       x.mark(kPhFlip);
       const int a = sh.na;

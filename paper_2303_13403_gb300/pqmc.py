@@ -37,7 +37,7 @@ class Opts(C.Structure):
     _fields_ = [("n_stab", C.c_int), ("delay_k", C.c_int), ("prec", C.c_int), ("seed", C.c_uint64),
                 ("n_chains", C.c_int), ("chain_offset", C.c_int), ("accept_log", C.c_int),
                 ("max_meas", C.c_int), ("stream", C.c_void_p), ("cta_threads", C.c_int), ("dense_chains", C.c_int),
-                ("dg_fp64", C.c_int)]
+                ("dg_fp64", C.c_int), ("spread", C.c_int)]
 
 
 # columns of a measurement record: sign of the weight, E/site, docc/site,
@@ -160,14 +160,15 @@ class Context:
     """One libpqmc context: a batch of chains on the GPU."""
 
     def __init__(self, specs, prec=FP64, seed=1, n_stab=10, delay_k=32, chain_offset=0, accept_log=0,
-                 max_meas=0, stream=None, cta_threads=0, dense_chains=0, dg_fp64=0):
+                 max_meas=0, stream=None, cta_threads=0, dense_chains=0, dg_fp64=0, spread=0):
         """delay_k = 0 lets the library's autotuner pick the delayed-update
-        block (and the CTA shape when cta_threads is 0)."""
+        block (and the CTA shape when cta_threads is 0); spread = 1 sweeps a
+        few large chains with grid-wide kernels (pqmc_opts.spread)."""
         lib = load()
         specs = list(specs)
         arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
         opts = Opts(n_stab, delay_k, prec, seed, len(specs), chain_offset, accept_log, max_meas,
-                    C.c_void_p(stream) if stream else None, cta_threads, dense_chains, dg_fp64)
+                    C.c_void_p(stream) if stream else None, cta_threads, dense_chains, dg_fp64, spread)
         h = C.c_void_p()
         _check(lib.pqmc_init_batch(len(specs), arr, C.byref(opts), C.byref(h)))
         self._h = h
@@ -329,7 +330,7 @@ def autotune(specs, prec=FP64, n_stab=10, delay_k=0, cta_threads=0, dense_chains
     lib = load()
     specs = list(specs)
     arr = (ChainSpec * len(specs))(*[chain_spec_of(s) for s in specs])
-    opts = Opts(n_stab, delay_k, prec, seed, len(specs), 0, 0, 0, None, cta_threads, dense_chains, 0)
+    opts = Opts(n_stab, delay_k, prec, seed, len(specs), 0, 0, 0, None, cta_threads, dense_chains, 0, 0)
     t = Tune()
     _check(lib.pqmc_autotune(len(specs), arr, C.byref(opts), C.byref(t)))
     return t.as_dict()
@@ -338,12 +339,12 @@ def autotune(specs, prec=FP64, n_stab=10, delay_k=0, cta_threads=0, dense_chains
 PROBE_KEYS = ("fp64_fma_tflops", "fp64_dmma_tflops", "fp32_fma_tflops", "fp64_fma_latency_cycles",
               "fp64_div_latency_cycles", "fp64_sqrt_latency_cycles", "fp64_warp_instr_cycles_1_lane",
               "fp64_warp_instr_cycles_8_lanes", "fp64_warp_instr_cycles_16_lanes", "fp64_warp_instr_cycles_32_lanes",
-              "sms", "sm_clock_mhz")
+              "sms", "sm_clock_mhz", "fp64_fma_dmma_mix_tflops", "fp64_fma_dmma_mix_time_ratio")
 
 
 def probe_pipes():
     """pqmc_probe_pipes: FP64 / DMMA / FP32 throughput and FP64 latencies of the current GPU."""
-    out = (C.c_double * 12)()
+    out = (C.c_double * 14)()
     _check(load().pqmc_probe_pipes(out))
     return dict(zip(PROBE_KEYS, list(out)))
 
