@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cta-threads", type=int, default=0, help="threads per chain CTA (0: autotuned)")
     ap.add_argument("--delay-k", type=int, default=0, help="delayed-update block (0: autotuned)")
+    ap.add_argument("--large-sweeps", type=int, default=3,
+                    help="timed sweeps of the single 648-site chain swept by the whole GPU (0: skip)")
     return ap.parse_args()
 
 
@@ -391,6 +393,36 @@ def run_ours(a):
                           "relative: divided by max(1, max|G_FP64|) per spin")
         return out
 
+    def large_chain(name, n_stab_, sweeps, warmup=2):
+        """One 648-site chain (18x18 honeycomb, 2 Theta = 20) swept by the
+        whole GPU (opts.spread): context creation, `warmup` sweeps (one
+        captured graph per sweep direction), then `sweeps` sweeps timed with
+        CUDA events."""
+        lspec = workloads.honeycomb(18, U=4.0, dtau=0.1, two_theta=20.0, g=0.6, M_N=0.21)
+        t0 = time.perf_counter()
+        ctx = pqmc.Context([lspec], prec=PRECS[name], seed=7, n_stab=n_stab_, stream=stream.cuda_stream, spread=1)
+        ctx.synchronize()
+        t_init = time.perf_counter() - t0
+        ctx.sweep(warmup, measure=False)
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = ctx.launch_count()
+        e0.record(stream)
+        ctx.sweep(sweeps, measure=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / sweeps
+        d = ctx.dims(0)
+        obs = ctx.measure(0)
+        errs = ctx.stab_errors(0, cap=4096)
+        out = {"ms_per_sweep": ms, "updates_per_s": (d["Ltau"] + 2) * d["N"] / (ms / 1e3), "n_stab": n_stab_,
+               "context_creation_s": t_init, "kernels_per_sweep": (ctx.launch_count() - n0) / sweeps,
+               "E_per_site_last_sweeps": float(np.mean(ctx.measurements(0)[-sweeps:, 1])),
+               "accept": obs["accept"], "max_dG": float(np.max(errs)) if len(errs) else None,
+               "dG_median": float(np.median(errs)) if len(errs) else None}
+        ctx.close()
+        return out
+
     head = a.prec
     n_stab = a.n_stab or NSTAB[head]
     r = timed(head, n_stab, a.steps, a.warmup, clocks=True)
@@ -420,6 +452,15 @@ def run_ours(a):
             for name, v in tts.items():
                 v["dE_vs_fp64_sigma"] = (v["E_per_site"] - ref["E_per_site"]) / float(
                     np.hypot(v["E_err"], ref["E_err"])) if name != "fp64" else 0.0
+    large = {}
+    if a.large_sweeps > 0:
+        for name, ns in (("fp32", 2), ("bf16x3", 2), ("fp64", 10)):
+            try:
+                large[name] = large_chain(name, ns, a.large_sweeps)
+            except pqmc.PQMCError as ex:
+                large[name] = {"error": str(ex)}
+        large["workload"] = ("one chain, 18x18 honeycomb (648 sites), U=4, g=0.6, M_N=0.21, 2Theta=20 "
+                             "(202 slices), swept by grid-wide kernel sequences (opts.spread)")
     dg64 = {}
     if a.dg_chains > 0 and rank == 0:
         for name in ("fp32", "bf16x3"):
@@ -490,6 +531,7 @@ def run_ours(a):
         "E_per_site": res["E_per_site"], "E_err": res["E_err"], "accept": res["accept"],
         "dG_per_stabilisation": res["dG_per_stabilisation"],
         "dG_vs_fp64_per_stabilisation": dg64,
+        "large_chain": large,
         "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": fp64_achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "sweep_kernel",
                      "pipe": "fp64",

@@ -524,9 +524,14 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   if (e == cudaSuccess) e = upload_run_order(ctx);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int), ctx->stream);
   if (e == cudaSuccess) e = prepare_sweep(ctx->prec, ctx->tpb, ctx->boost, ctx->res_bytes);
+  if (e == cudaSuccess && ctx->spread) e = spread_prepare();
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "upload"); }
-  e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream, -1);
-  ctx->launches++;
+  if (ctx->spread) {
+    e = spread_init(ctx->plan, ctx->stream);
+  } else {
+    e = launch_init(ctx->prec, ctx->tpb, ctx->boost, ctx->d_desc, 0, n, o.seed, ctx->res_bytes, ctx->d_err, ctx->stream, -1);
+    ctx->launches++;
+  }
   if (e != cudaSuccess) { pqmc_free(ctx); return cuda_fail(nullptr, e, "init launch"); }
   pqmc_status st = sync_check(ctx);
   if (st != PQMC_OK) { g_init_error = ctx->err; pqmc_free(ctx); return st; }

@@ -186,16 +186,17 @@ PQMC_HDI ScratchLayout scratch_layout(int N, int ld, int n, int tsize, int kd) {
 //   xt, qrt, qlt: path-precision copies of O^{-1} (n x n), Q_R and Q_L (N x n, ld N)
 //   y[s]        : n x ld (T) O^{-1} Q_L^T
 //   gt[s]       : N x ld (T) wrap intermediate
-//   u, w, mb    : U = E_S - G_{:,S} (N x kBlock, ld N), W = G_{S,:} (kBlock x ld) and
-//                 M (kBlock x kBlock) of the flips accepted in one block
+//   g2          : 2 x N x ld (T) second copy of G: the block updates of a slice
+//                 alternate between G and g2 (read one, write the other)
+//   mb[s]       : M (kBlock x kBlock, T) of the flips accepted in one block
 //   misc        : int na (accepted flips of the block), int bad[2] (Cholesky
 //                 breakdown), then 8-aligned: uint64 dmax (bits of max |G - G_fresh|),
-//                 double lchol[2] (log det R)
+//                 double lchol[2] (log det R); at 64: int sites[kBlock] (accepted sites)
 constexpr int kSpPanel = 32;   // Cholesky panel width
 constexpr int kSpGJ = 16;      // Gauss-Jordan panel width
 struct SpreadLayout {
   size_t mt[2][2], m64[2], c64[2], rinv[2], o64[2], tgj[2], pval[2], perm[2], d0[2], xt[2], qrt[2], qlt[2], y[2],
-      gt[2], u[2], w[2], mb[2], misc, total;
+      gt[2], mb[2], g2, misc, total;
 };
 
 PQMC_HDI SpreadLayout spread_layout(int N, int ld, int n, int tsize) {
@@ -223,11 +224,10 @@ PQMC_HDI SpreadLayout spread_layout(int N, int ld, int n, int tsize) {
     L.qlt[s] = take(Nn * tsize);
     L.y[s] = take((size_t)n * ld * tsize);
     L.gt[s] = take((size_t)N * ld * tsize);
-    L.u[s] = take((size_t)N * kBlock * tsize);
-    L.w[s] = take((size_t)kBlock * ld * tsize);
     L.mb[s] = take((size_t)kBlock * kBlock * tsize);
   }
-  L.misc = take(64);
+  L.g2 = take(2 * (size_t)N * ld * tsize);
+  L.misc = take(64 + kBlock * 4);
   L.total = off;
   return L;
 }

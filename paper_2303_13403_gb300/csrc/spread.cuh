@@ -8,9 +8,11 @@
 //
 //   per block of kBlock sites   sp_decide (one CTA per chain: the Metropolis
 //                               decisions of decide_sub_block, then the block
-//                               form's M = Gamma (1 + (1 - G_SS) Gamma)^{-1},
-//                               U = E_S - G_{:,S}, W = G_{S,:}),
-//                               sp_flush (tiles of G: G -= U (M W))
+//                               form's M = Gamma (1 + (1 - G_SS) Gamma)^{-1}),
+//                               sp_flush (tiles of G: G_new = G - (E_S - G_{:,S})
+//                               M G_{S,:}, read from one copy of G and written
+//                               to the other, so no tile reads what another
+//                               tile writes)
 //   per slice                   sp_scale (e^{V} G e^{-V}), two tile products
 //                               with e^{-+dtau K} (the wrap)
 //   per stabilisation           the n_stab slice products of the new stack
@@ -44,6 +46,7 @@ struct SpJob {
   const void* B;
   void* C;
   unsigned long long* dmax;   // kSpFresh: max |G - G_fresh| of the chain (bits of a non-negative double)
+  const void* Cin;            // kSpFresh: the propagated G to compare with (same layout as C; null: C)
   int M, Nn, K;
   int p1;                     // kSpGJUpd: end of the panel block row
 };
@@ -54,6 +57,7 @@ struct SpGemm {
   int tiles_n;                // tiles along the columns of the largest job
   int split;                  // BF16X3 wrap products (T = float)
   int p0;                     // kSpGJUpd: start of the panel block row
+  int upper;                  // 1: only tiles that reach the upper triangle (j >= i) are computed
   int njobs;
   SpJob job[kSpMaxJobs];
 };
@@ -61,6 +65,8 @@ struct SpGemm {
 template <typename T> struct SpTile;
 template <> struct SpTile<float> { static constexpr int TM = 64, TK = 16, R = 4; };
 template <> struct SpTile<double> { static constexpr int TM = 32, TK = 32, R = 2; };
+// the Cholesky block row is formed in place by one K slice per tile
+static_assert(kSpPanel <= SpTile<double>::TK && kSpPanel <= SpTile<double>::TM, "block row in one tile slice");
 
 // One TM x TM tile of C per CTA (256 threads, R x R outputs each, rows and
 // columns interleaved by 16), operands staged through shared memory in
@@ -73,7 +79,7 @@ __global__ void __launch_bounds__(256) sp_gemm_kernel(SpGemm g) {
   __shared__ double red[8];
   const SpJob& jb = g.job[blockIdx.y];
   const int r0 = (blockIdx.x / g.tiles_n) * TM, c0 = (blockIdx.x % g.tiles_n) * TM;
-  if (r0 >= jb.M || c0 >= jb.Nn) return;
+  if (r0 >= jb.M || c0 >= jb.Nn || (g.upper && r0 > c0 + TM - 1)) return;
   const T* A = static_cast<const T*>(jb.A);
   const T* B = static_cast<const T*>(jb.B);
   T* C = static_cast<T*>(jb.C);
@@ -107,8 +113,9 @@ __global__ void __launch_bounds__(256) sp_gemm_kernel(SpGemm g) {
       Bs[k][j] = (gj < jb.Nn && gk < jb.K) ? B[(long)gk * g.sbk + (long)gj * g.sbj] : T(0);
     }
     __syncthreads();
+    const int kt = min(TK, jb.K - k0);   // no FMAs on the zero padding (FP64 issue is scarce)
 #pragma unroll 4
-    for (int k = 0; k < TK; ++k) {
+    for (int k = 0; k < kt; ++k) {
       T a[R], b[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) a[r] = As[k][ty + 16 * r];
@@ -136,7 +143,8 @@ __global__ void __launch_bounds__(256) sp_gemm_kernel(SpGemm g) {
       } else if constexpr (kMode == kSpFresh) {
         // G_fresh = delta_ij - (Q_R Y)_ij against the propagated G
         const T gnew = (i == j ? T(1) : T(0)) - acc[r][q];
-        const T d = fabs(ref - gnew);
+        const T gold = jb.Cin ? static_cast<const T*>(jb.Cin)[(long)i * g.sci + (long)j * g.scj] : ref;
+        const T d = fabs(gold - gnew);
         dm = d == d ? fmax(dm, (double)d) : INFINITY;   // a NaN is recorded as +inf
         ref = gnew;
       } else {
@@ -184,9 +192,9 @@ struct SpBuf {
   __device__ __host__ T* qlt(int s) const { return reinterpret_cast<T*>(b + L.qlt[s]); }
   __device__ __host__ T* y(int s) const { return reinterpret_cast<T*>(b + L.y[s]); }
   __device__ __host__ T* gt(int s) const { return reinterpret_cast<T*>(b + L.gt[s]); }
-  __device__ __host__ T* u(int s) const { return reinterpret_cast<T*>(b + L.u[s]); }
-  __device__ __host__ T* w(int s) const { return reinterpret_cast<T*>(b + L.w[s]); }
   __device__ __host__ T* mb(int s) const { return reinterpret_cast<T*>(b + L.mb[s]); }
+  __device__ __host__ T* g2() const { return reinterpret_cast<T*>(b + L.g2); }
+  __device__ __host__ int* sites() const { return reinterpret_cast<int*>(b + L.misc + 64); }
   __device__ __host__ int* na() const { return reinterpret_cast<int*>(b + L.misc); }
   __device__ __host__ int* bad() const { return reinterpret_cast<int*>(b + L.misc) + 1; }
   __device__ __host__ unsigned long long* dmax() const {
@@ -204,98 +212,151 @@ __device__ __forceinline__ double sp_vexp(const ChainDesc& c, int tau, int s, in
 // ---------------------------------------------------------------------------
 // Flips of one block: decisions, then the factors of the block update.
 
+// The current G of a chain: its own buffer (alt = 0) or the second copy.
+template <typename T>
+__device__ __forceinline__ T* sp_gcur(const ChainDesc& c, int alt, int tsize = (int)sizeof(T)) {
+  return alt ? SpBuf<T>(c.spread, c.N, c.ld, c.nmax, tsize).g2() : static_cast<T*>(c.G);
+}
+
+// Decisions of block [i0, i0 + kBlock) on the current G (one CTA per chain),
+// then M = Gamma (1 + (1 - G_SS) Gamma)^{-1} and the accepted sites.
 template <typename T>
 __global__ void __launch_bounds__(256) sp_decide_kernel(const ChainDesc* chains, uint64_t seed,
-                                                        const uint32_t* sweep_ctr, int tau, int i0, int* err) {
+                                                        const uint32_t* sweep_ctr, int tau, int i0, int alt, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (chains[blockIdx.x].st->err) return;
   Cta<T> x = make_cta<T>(chains[blockIdx.x], smem_raw, 0, seed);
   load_state(x);
   const ChainDesc& c = x.c;
-  const int N = c.N, ld = c.ld;
-  decide_sub_block(x, tau, *sweep_ctr, i0, min(kBlock, N - i0), 0);
+  x.Gp = sp_gcur<T>(c, alt);
+  decide_sub_block(x, tau, *sweep_ctr, i0, min(kBlock, c.N - i0), 0);
   __syncthreads();
   x.mark(kPhFlip);
   const int a = x.sh.na;
-  SpBuf<T> sp(c.spread, N, ld, c.nmax);
+  SpBuf<T> sp(c.spread, c.N, c.ld, c.nmax);
   if (threadIdx.x == 0) *sp.na() = a;
   if (a > 0) {
     FlipBuf<T>& fb = *x.fb;
     block_inverse(x, a, false);
+    if ((int)threadIdx.x < a) sp.sites()[threadIdx.x] = fb.gsite[threadIdx.x];
     for (int s = 0; s < 2; ++s) {
-      const T* Gs = x.G(s);
       T* Mb = sp.mb(s);
-      T* U = sp.u(s);
-      T* W = sp.w(s);
       PQMC_FOR_2D(l, 0, a, m, 0, a) Mb[l * kBlock + m] = fb.Tu[s][l][m];
-      PQMC_FOR_2D(m, 0, a, i, 0, N) {
-        const int col = fb.gsite[m];
-        U[(long)m * N + i] = (i == col ? T(1) : T(0)) - Gs[(long)i * ld + col];
-      }
-      PQMC_FOR_2D(l, 0, a, q, 0, N) W[(long)l * ld + q] = Gs[(long)fb.gsite[l] * ld + q];
     }
   }
   x.mark(kPhFlush);
   store_state(x, err);
 }
 
-// G_s -= U (M W) on one 64 x 64 tile of G per CTA (grid: tiles, spin, chain)
+// Block update on one 64 x 64 tile of G per CTA (grid: tiles, spin, chain):
+// G_new = G_old - (E_S - G_old[:, S]) M G_old[S, :], G_old the current buffer
+// (alt), G_new the other one; a copy when no flip was accepted.
 template <typename T>
-__global__ void __launch_bounds__(256) sp_flush_kernel(const ChainDesc* chains) {
+__global__ void __launch_bounds__(256) sp_flush_kernel(const ChainDesc* chains, int i0, int alt) {
   constexpr int TT = 64;
   __shared__ T Ms[kBlock][kBlock + 1];
   __shared__ T MW[kBlock][TT];
+  __shared__ T Ws[kBlock][TT];
   __shared__ T Us[TT][kBlock + 1];
+  __shared__ int st[kBlock];
   const ChainDesc& c = chains[blockIdx.z];
   if (c.st->err) return;
   const int N = c.N, ld = c.ld, s = blockIdx.y;
   SpBuf<T> sp(c.spread, N, ld, c.nmax);
+  const T* Gin = sp_gcur<T>(c, alt) + (long)s * N * ld;
+  T* Gout = sp_gcur<T>(c, alt ^ 1) + (long)s * N * ld;
   const int a = *sp.na();
-  if (a == 0) return;
   const int tn = (N + TT - 1) / TT;
   const int r0 = (blockIdx.x / tn) * TT, c0 = (blockIdx.x % tn) * TT;
   if (r0 >= N) return;
   const int nr = min(TT, N - r0), nc = min(TT, N - c0);
+  if (a == 0) {
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      const long o = (long)(r0 + e / nc) * ld + c0 + e % nc;
+      Gout[o] = Gin[o];
+    }
+    return;
+  }
   const T* Mb = sp.mb(s);
-  const T* U = sp.u(s);
-  const T* W = sp.w(s);
+  if ((int)threadIdx.x < a) st[threadIdx.x] = sp.sites()[threadIdx.x];
   for (int e = threadIdx.x; e < a * a; e += blockDim.x) Ms[e / a][e % a] = Mb[(e / a) * kBlock + e % a];
+  __syncthreads();
+  // W = G_old[S, tile columns]; U = E_S - G_old[tile rows, S]
+  for (int e = threadIdx.x; e < a * nc; e += blockDim.x) {
+    const int l = e / nc, j = e % nc;
+    Ws[l][j] = Gin[(long)st[l] * ld + c0 + j];
+  }
   for (int e = threadIdx.x; e < a * nr; e += blockDim.x) {
-    const int m = e / nr, i = e % nr;
-    Us[i][m] = U[(long)m * N + r0 + i];
+    const int i = e / a, m = e % a;
+    Us[i][m] = (r0 + i == st[m] ? T(1) : T(0)) - Gin[(long)(r0 + i) * ld + st[m]];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < a * nc; e += blockDim.x) {
     const int l = e / nc, j = e % nc;
     T v = T(0);
-    for (int m = 0; m < a; ++m) v = fma(Ms[l][m], W[(long)m * ld + c0 + j], v);
+    for (int m = 0; m < a; ++m) v = fma(Ms[l][m], Ws[m][j], v);
     MW[l][j] = v;
   }
   __syncthreads();
-  T* G = static_cast<T*>(c.G) + (long)s * N * ld;
-  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-    const int i = e / nc, j = e % nc;
-    T v = T(0);
-    for (int m = 0; m < a; ++m) v = fma(Us[i][m], MW[m][j], v);
-    G[(long)(r0 + i) * ld + c0 + j] -= v;
+  // 4 x 4 outputs per thread, rows and columns interleaved by 16
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
+  for (int m = 0; m < a; ++m) {
+    T u[4], w[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) u[r] = Us[ty + 16 * r][m];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = MW[m][tx + 16 * q];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = fma(u[r], w[q], acc[r][q]);
   }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ty + 16 * r, j = tx + 16 * q;
+      if (i < nr && j < nc) {
+        const long o = (long)(r0 + i) * ld + c0 + j;
+        Gout[o] = Gin[o] - acc[r][q];
+      }
+    }
+  (void)i0;
+}
+
+// G (both spins) from the second copy back into the chain's own buffer
+template <typename T>
+__global__ void sp_copy_back_kernel(const ChainDesc* chains) {
+  const ChainDesc& c = chains[blockIdx.z];
+  if (c.st->err) return;
+  const long n = 2L * c.N * c.ld;
+  const T* src = SpBuf<T>(c.spread, c.N, c.ld, c.nmax).g2();
+  T* dst = static_cast<T*>(c.G);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) dst[e] = src[e];
 }
 
 // ---------------------------------------------------------------------------
 // Diagonal factors of a slice.
 
-// G_s <- e^{V} G_s e^{-V} (dir > 0) or e^{-V} G_s e^{V} (dir < 0)
+// G_s <- e^{V} G_s e^{-V} (dir > 0) or e^{-V} G_s e^{V} (dir < 0), read from
+// the current buffer (alt), written to the chain's own
 template <typename T>
-__global__ void sp_scale_kernel(const ChainDesc* chains, int tau, int dir) {
+__global__ void sp_scale_kernel(const ChainDesc* chains, int tau, int dir, int alt) {
   const ChainDesc& c = chains[blockIdx.z];
   if (c.st->err) return;
   const int N = c.N, ld = c.ld, s = blockIdx.y;
+  const T* Gin = sp_gcur<T>(c, alt) + (long)s * N * ld;
   T* G = static_cast<T*>(c.G) + (long)s * N * ld;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
     const int i = (int)(e / N), j = (int)(e % N);
     const double vi = sp_vexp(c, tau, s, i), vj = sp_vexp(c, tau, s, j);
     const T f = dir > 0 ? (T)vi * (T)(1.0 / vj) : (T)vj * (T)(1.0 / vi);
-    G[(long)i * ld + j] *= f;
+    G[(long)i * ld + j] = Gin[(long)i * ld + j] * f;
   }
 }
 
@@ -379,12 +440,36 @@ __global__ void sp_cvt_kernel(const ChainDesc* chains, int b) {
   }
 }
 
-// End of a stabilisation, one CTA per chain: the stack block's weight
-// (log|det R| and the previous block's), the weight of G from O's pivots,
-// the recorded max |G - G_fresh|, and the measurement when asked.
+// Weight of stack block b just factorised (one thread per spin, chain):
+// log|det| of the previous block plus log det R (R has a positive diagonal,
+// so the sign is the previous block's); a Cholesky breakdown stops the chain.
+static __global__ void sp_stack_log_kernel(const ChainDesc* chains, int b, int left, int tsize, int* err) {
+  const ChainDesc& c = chains[blockIdx.x];
+  const int s = threadIdx.x;
+  if (s >= 2 || c.st->err) return;
+  const SpBuf<double> sp(c.spread, c.N, c.ld, c.nmax, tsize);
+  double* lg = left ? c.Llog : c.Rlog;
+  const bool first = left ? b == c.nb : b == 0;
+  const int bp = left ? b + 1 : b - 1;
+  const double prev_l = first ? 0.0 : lg[(bp * 2 + s) * 2 + 0];
+  const double prev_s = first ? 1.0 : lg[(bp * 2 + s) * 2 + 1];
+  lg[(b * 2 + s) * 2 + 0] = prev_l + sp.lchol()[s];
+  lg[(b * 2 + s) * 2 + 1] = prev_s;
+  if (sp.bad()[s]) {
+    atomicOr(&c.st->err, kErrStab);
+    atomicOr(err, kErrStab);
+  }
+}
+
+// End of a stabilisation, one CTA per chain: the weight of G from the stack
+// blocks' weights and O's pivots,
+// the recorded max |G - G_fresh| (flags & kSpRecord), the measurement
+// (flags & kSpMeasure), or at initialisation the running sign from the
+// weight (flags & kSpInit).
+enum : int { kSpMeasure = 1, kSpRecord = 2, kSpInit = 4 };
 template <typename T>
 __global__ void __launch_bounds__(256) sp_tail_kernel(const ChainDesc* chains, uint64_t seed, int b, int left,
-                                                      int do_measure, int* err) {
+                                                      int flags, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (chains[blockIdx.x].st->err) return;
   Cta<T> x = make_cta<T>(chains[blockIdx.x], smem_raw, 0, seed);
@@ -395,17 +480,7 @@ __global__ void __launch_bounds__(256) sp_tail_kernel(const ChainDesc* chains, u
   double sign_total = 1.0;
   for (int s = 0; s < 2; ++s) {
     const int n = x.nsig(s);
-    // stack block b of this stabilisation
-    if (threadIdx.x == 0) {
-      double* lg = left ? c.Llog : c.Rlog;
-      const bool first = left ? b == c.nb : b == 0;
-      const int bp = left ? b + 1 : b - 1;
-      const double prev_l = first ? 0.0 : lg[(bp * 2 + s) * 2 + 0];
-      const double prev_s = first ? 1.0 : lg[(bp * 2 + s) * 2 + 1];
-      lg[(b * 2 + s) * 2 + 0] = prev_l + sp.lchol()[s];
-      lg[(b * 2 + s) * 2 + 1] = prev_s;
-      if (sp.bad()[s]) sh.err |= kErrStab;
-    }
+    if (threadIdx.x == 0 && sp.bad()[s]) sh.err |= kErrStab;   // a zero Gauss-Jordan pivot
     __syncthreads();
     // row interchanges of the Gauss-Jordan inverse
     int sw = 0;
@@ -425,14 +500,17 @@ __global__ void __launch_bounds__(256) sp_tail_kernel(const ChainDesc* chains, u
   if (threadIdx.x == 0) {
     const double dmax = __longlong_as_double((long long)*sp.dmax());
     *sp.dmax() = 0ull;
-    if (!isfinite(dmax)) sh.err |= kErrNaN;
-    sh.dGmax = fmax(sh.dGmax, dmax);
-    c.dG[c.st->n_dG % kDGHistory] = dmax;
-    c.st->n_dG++;
+    if (flags & kSpRecord) {
+      if (!isfinite(dmax)) sh.err |= kErrNaN;
+      sh.dGmax = fmax(sh.dGmax, dmax);
+      c.dG[c.st->n_dG % kDGHistory] = dmax;
+      c.st->n_dG++;
+    }
+    if (flags & kSpInit) sh.sign_running = sh.sign_spin[0] * sh.sign_spin[1];
     c.st->sign_stack = sign_total;
   }
   __syncthreads();
-  if (do_measure) measure(x);
+  if (flags & kSpMeasure) measure(x);
   store_state(x, err);
 }
 
@@ -442,15 +520,15 @@ __global__ void __launch_bounds__(256) sp_tail_kernel(const ChainDesc* chains, u
 
 // FP64 tile product over the jobs of g
 cudaError_t sp_dgemm(SpGemm& g, int mode, int max_m, int max_n, cudaStream_t st);
-// Cholesky factor C = R^T R, panel p: the diagonal block, then the block row
-// R_{P,rest} = R_PP^{-T} C_{P,rest} (the trailing update is an sp_dgemm)
+// Cholesky factor C = R^T R, panel p: the diagonal block R_PP and its inverse
+// (the block row R_{P,rest} = R_PP^{-T} C_{P,rest} and the trailing update
+// are sp_dgemm products)
 cudaError_t sp_chol_panel(const ChainDesc* d, int nc, int nmax, int p, int tsize, cudaStream_t st);
-cudaError_t sp_chol_rows(const ChainDesc* d, int nc, int nmax, int p, int tsize, cudaStream_t st);
-// inverses of the diagonal blocks of R, then Q = M R^{-1} into stack block b
+// Q = M R^{-1} into stack block b
 cudaError_t sp_qform(const ChainDesc* d, int nc, int N, int nmax, int left, int b, int tsize, cudaStream_t st);
 // Gauss-Jordan panel p of O (pivots, row interchanges, the panel's columns,
 // the saved block row), and the interchanges undone on the columns at the end
-cudaError_t sp_gj_panel(const ChainDesc* d, int nc, int p, int tsize, cudaStream_t st);
+cudaError_t sp_gj_panel(const ChainDesc* d, int nc, int nmax, int p, int tsize, cudaStream_t st);
 cudaError_t sp_gj_unswap(const ChainDesc* d, int nc, int nmax, int tsize, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
@@ -471,8 +549,12 @@ cudaError_t sp_gemm_t(SpGemm& g, int mode, int max_m, int max_n, cudaStream_t st
   return cudaGetLastError();
 }
 
+// mode 0: an up sweep, 1: a down sweep (measure at the middle slice when
+// measure != 0); 2: the initialisation from the chains' fields (the left
+// stack, right block 0, G at tau = -1 and the running sign), the same steps
+// as the single-CTA initialisation
 template <typename T>
-cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStream_t st) {
+cudaError_t spread_sweep_t(const SpreadPlan& P, int mode, int measure, cudaStream_t st) {
   const int nc = P.n, N = P.N, ld = P.ld, ldn = P.nmax, ts = (int)sizeof(T);
   const int nsig[2] = {P.nup, P.ndn};
   const int split = (std::is_same<T, float>::value && P.prec == PQMC_BF16X3) ? 1 : 0;
@@ -488,6 +570,10 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
   };
   auto buf = [&](int c) { return SpBuf<T>(P.ch[c].sp, N, ld, P.nmax); };
   auto Gs = [&](int c, int s) { return static_cast<T*>(P.ch[c].G) + (long)s * N * ld; };
+  // the block updates of a slice alternate between the chain's G and its
+  // second copy; cur = 1 while the current G is the copy
+  int cur = 0;
+  auto Gcur = [&](int c, int s) { return (cur ? buf(c).g2() : static_cast<T*>(P.ch[c].G)) + (long)s * N * ld; };
   auto stack_block = [&](int c, bool left, int b, int s) {
     return (left ? P.ch[c].Lst : P.ch[c].Rst) + ((long)b * 2 + s) * N * P.nmax;
   };
@@ -496,17 +582,20 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
   auto update = [&](int tau) {
     const int tn = (N + 63) / 64;
     for (int i0 = 0; i0 < N && e == cudaSuccess; i0 += kBlock) {
-      sp_decide_kernel<T><<<nc, 256, smem_cta, st>>>(D, P.seed, P.d_sweep, tau, i0, P.d_err);
+      sp_decide_kernel<T><<<nc, 256, smem_cta, st>>>(D, P.seed, P.d_sweep, tau, i0, cur, P.d_err);
       ok(cudaSuccess);
-      sp_flush_kernel<T><<<dim3(tn * tn, 2, nc), 256, 0, st>>>(D);
+      sp_flush_kernel<T><<<dim3(tn * tn, 2, nc), 256, 0, st>>>(D, i0, cur);
       ok(cudaSuccess);
+      cur ^= 1;
     }
   };
   auto wrap = [&](int tau, int dir) {
     const bool gz = tau == 0 || tau == P.Ltau + 1;
-    if (dir > 0) {
-      sp_scale_kernel<T><<<ew, 256, 0, st>>>(D, tau, +1);
+    // every path through the wrap ends with G in the chain's own buffer
+    if (dir > 0 || gz) {
+      sp_scale_kernel<T><<<ew, 256, 0, st>>>(D, tau, dir, cur);
       ok(cudaSuccess);
+      cur = 0;
     }
     if (!gz) {
       // Gt = E1 G, G = Gt E2: (E1, E2) = (e^{-dtau K}, e^{+dtau K}) up, reversed down;
@@ -520,15 +609,16 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
         for (int s = 0; s < 2; ++s) {
           const void* E1 = dir > 0 ? P.ch[c].expKm : P.ch[c].expKp;
           const void* E2 = dir > 0 ? P.ch[c].expKp : P.ch[c].expKm;
-          g1.job[2 * c + s] = SpJob{E1, Gs(c, s), buf(c).gt(s), nullptr, N, N, N, 0};
-          g2.job[2 * c + s] = SpJob{buf(c).gt(s), E2, Gs(c, s), nullptr, N, N, N, 0};
+          g1.job[2 * c + s] = SpJob{E1, Gcur(c, s), buf(c).gt(s), nullptr, nullptr, N, N, N, 0};
+          g2.job[2 * c + s] = SpJob{buf(c).gt(s), E2, Gs(c, s), nullptr, nullptr, N, N, N, 0};
         }
       ok(sp_gemm_t<T>(g1, kSpStore, N, N, st));
       ok(sp_gemm_t<T>(g2, kSpStore, N, N, st));
-    }
-    if (dir < 0) {
-      sp_scale_kernel<T><<<ew, 256, 0, st>>>(D, tau, -1);
-      ok(cudaSuccess);
+      cur = 0;
+      if (dir < 0) {
+        sp_scale_kernel<T><<<ew, 256, 0, st>>>(D, tau, -1, 0);
+        ok(cudaSuccess);
+      }
     }
   };
   // stack block b (right: from block b-1, left: from block b+1) and its QR
@@ -547,7 +637,7 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
         g.sai = 1; g.sak = ld; g.sbk = ldn; g.sbj = 1; g.sci = ldn; g.scj = 1;
         for (int c = 0; c < nc; ++c)
           for (int s = 0; s < 2; ++s)
-            g.job[2 * c + s] = SpJob{P.ch[c].expKm, buf(c).mt(s, cur), buf(c).mt(s, cur ^ 1), nullptr, N, nsig[s], N, 0};
+            g.job[2 * c + s] = SpJob{P.ch[c].expKm, buf(c).mt(s, cur), buf(c).mt(s, cur ^ 1), nullptr, nullptr, N, nsig[s], N, 0};
         ok(sp_gemm_t<T>(g, kSpStore, N, ldn, st));
         cur ^= 1;
       };
@@ -572,34 +662,55 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
       SpGemm g{};
       g.njobs = 2 * nc;
       g.sai = N; g.sak = 1; g.sbk = 1; g.sbj = N; g.sci = ldn; g.scj = 1;
+      g.upper = 1;   // the factorisation reads the upper triangle only
       for (int c = 0; c < nc; ++c)
         for (int s = 0; s < 2; ++s)
-          g.job[2 * c + s] = SpJob{buf(c).m64(s), buf(c).m64(s), buf(c).c64(s), nullptr, nsig[s], nsig[s], N, 0};
+          g.job[2 * c + s] = SpJob{buf(c).m64(s), buf(c).m64(s), buf(c).c64(s), nullptr, nullptr, nsig[s], nsig[s], N, 0};
       ok(sp_dgemm(g, kSpStore, ldn, ldn, st));
     }
     for (int p0 = 0; p0 < ldn && e == cudaSuccess; p0 += kSpPanel) {
       const int p = p0 / kSpPanel;
       ok(sp_chol_panel(D, nc, ldn, p, ts, st));
-      ok(sp_chol_rows(D, nc, ldn, p, ts, st));
+      {
+        // block row in place: R_{P,rest} = R_PP^{-T} C_{P,rest} (a single
+        // K slice, so every tile reads its columns before it writes them)
+        SpGemm r{};
+        r.njobs = 2 * nc;
+        r.sai = 1; r.sak = kSpPanel; r.sbk = ldn; r.sbj = 1; r.sci = ldn; r.scj = 1;
+        int maxr = 0;
+        for (int c = 0; c < nc; ++c)
+          for (int s = 0; s < 2; ++s) {
+            const int p1 = std::min(p0 + kSpPanel, nsig[s]);
+            const int rest = p0 < nsig[s] ? nsig[s] - p1 : 0;
+            double* C = buf(c).c64(s);
+            r.job[2 * c + s] = SpJob{buf(c).rinv(s) + (long)p * kSpPanel * kSpPanel, C + (long)p0 * ldn + p1,
+                                     C + (long)p0 * ldn + p1, nullptr, nullptr, rest > 0 ? p1 - p0 : 0, rest, p1 - p0, 0};
+            maxr = std::max(maxr, rest);
+          }
+        if (maxr > 0) ok(sp_dgemm(r, kSpStore, kSpPanel, maxr, st));
+      }
       SpGemm g{};
       g.njobs = 2 * nc;
       g.sai = 1; g.sak = ldn; g.sbk = ldn; g.sbj = 1; g.sci = ldn; g.scj = 1;
+      g.upper = 1;
       int maxr = 0;
       for (int c = 0; c < nc; ++c)
         for (int s = 0; s < 2; ++s) {
           const int p1 = std::min(p0 + kSpPanel, nsig[s]);
           const int rest = p0 < nsig[s] ? nsig[s] - p1 : 0;
           double* C = buf(c).c64(s);
-          g.job[2 * c + s] = SpJob{C + (long)p0 * ldn + p1, C + (long)p0 * ldn + p1, C + (long)p1 * ldn + p1, nullptr,
+          g.job[2 * c + s] = SpJob{C + (long)p0 * ldn + p1, C + (long)p0 * ldn + p1, C + (long)p1 * ldn + p1, nullptr, nullptr,
                                    rest, rest, p1 - p0, 0};
           maxr = std::max(maxr, rest);
         }
       if (maxr > 0) ok(sp_dgemm(g, kSpSub, maxr, maxr, st));
     }
     ok(sp_qform(D, nc, N, ldn, left ? 1 : 0, b, ts, st));
+    sp_stack_log_kernel<<<nc, 32, 0, st>>>(D, b, left ? 1 : 0, ts, P.d_err);
+    ok(cudaSuccess);
   };
   // G = 1 - Q_R (Q_L^T Q_R)^{-1} Q_L^T at stabilisation point b
-  auto refresh = [&](int b, bool left, int meas) {
+  auto refresh = [&](int b, bool left, int flags) {
     {
       SpGemm g{};
       g.njobs = 2 * nc;
@@ -607,11 +718,11 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
       for (int c = 0; c < nc; ++c)
         for (int s = 0; s < 2; ++s)
           g.job[2 * c + s] =
-              SpJob{stack_block(c, true, b, s), stack_block(c, false, b, s), buf(c).o64(s), nullptr, nsig[s], nsig[s], N, 0};
+              SpJob{stack_block(c, true, b, s), stack_block(c, false, b, s), buf(c).o64(s), nullptr, nullptr, nsig[s], nsig[s], N, 0};
       ok(sp_dgemm(g, kSpStore, ldn, ldn, st));
     }
     for (int p0 = 0; p0 < ldn && e == cudaSuccess; p0 += kSpGJ) {
-      ok(sp_gj_panel(D, nc, p0 / kSpGJ, ts, st));
+      ok(sp_gj_panel(D, nc, ldn, p0 / kSpGJ, ts, st));
       SpGemm g{};
       g.njobs = 2 * nc;
       g.p0 = p0;
@@ -620,7 +731,7 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
         for (int s = 0; s < 2; ++s) {
           const int n = nsig[s], p1 = std::min(p0 + kSpGJ, n);
           double* O = buf(c).o64(s);
-          g.job[2 * c + s] = SpJob{O + p0, buf(c).tgj(s), O, nullptr, p0 < n ? n : 0, n, p1 - p0, p1};
+          g.job[2 * c + s] = SpJob{O + p0, buf(c).tgj(s), O, nullptr, nullptr, p0 < n ? n : 0, n, p1 - p0, p1};
         }
       ok(sp_dgemm(g, kSpGJUpd, ldn, ldn, st));
     }
@@ -641,22 +752,28 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
         const void* X = f64 ? (const void*)B.o64(s) : (const void*)B.xt(s);
         const void* QL = f64 ? (const void*)stack_block(c, true, b, s) : (const void*)B.qlt(s);
         const void* QR = f64 ? (const void*)stack_block(c, false, b, s) : (const void*)B.qrt(s);
-        gy.job[2 * c + s] = SpJob{X, QL, B.y(s), nullptr, nsig[s], N, nsig[s], 0};
-        gg.job[2 * c + s] = SpJob{QR, B.y(s), Gs(c, s), B.dmax(), N, N, nsig[s], 0};
+        gy.job[2 * c + s] = SpJob{X, QL, B.y(s), nullptr, nullptr, nsig[s], N, nsig[s], 0};
+        gg.job[2 * c + s] = SpJob{QR, B.y(s), Gs(c, s), B.dmax(), Gcur(c, s), N, N, nsig[s], 0};
       }
     ok(sp_gemm_t<T>(gy, kSpStore, ldn, N, st));
     ok(sp_gemm_t<T>(gg, kSpFresh, N, N, st));
-    sp_tail_kernel<T><<<nc, 256, smem_cta, st>>>(D, P.seed, b, left ? 1 : 0, meas, P.d_err);
+    cur = 0;
+    sp_tail_kernel<T><<<nc, 256, smem_cta, st>>>(D, P.seed, b, left ? 1 : 0, flags, P.d_err);
     ok(cudaSuccess);
   };
 
-  if ((parity & 1) == 0) {
+  if (mode == 2) {
+    for (int b = P.nb; b >= 0 && e == cudaSuccess; --b) stack(b, true);
+    stack(0, false);
+    refresh(0, false, kSpInit);
+    wrap(0, -1);
+  } else if (mode == 0) {
     for (int tau = 0; tau <= P.Ltau + 1 && e == cudaSuccess; ++tau) {
       update(tau);
       wrap(tau, +1);
       if (tau <= P.Ltau && tau % P.n_stab == 0) {
         stack(tau / P.n_stab, false);
-        refresh(tau / P.n_stab, false, (measure && tau == P.Ltau / 2) ? 1 : 0);
+        refresh(tau / P.n_stab, false, kSpRecord | ((measure && tau == P.Ltau / 2) ? kSpMeasure : 0));
       }
     }
   } else {
@@ -666,9 +783,13 @@ cudaError_t spread_sweep_t(const SpreadPlan& P, int parity, int measure, cudaStr
       const int t1 = tau - 1;
       if (t1 >= 0 && t1 % P.n_stab == 0) {
         stack(t1 / P.n_stab, true);
-        refresh(t1 / P.n_stab, true, (measure && t1 == P.Ltau / 2) ? 1 : 0);
+        refresh(t1 / P.n_stab, true, kSpRecord | ((measure && t1 == P.Ltau / 2) ? kSpMeasure : 0));
       }
     }
+  }
+  if (cur && e == cudaSuccess) {
+    sp_copy_back_kernel<T><<<ew, 256, 0, st>>>(D);
+    ok(cudaSuccess);
   }
   return e;
 }

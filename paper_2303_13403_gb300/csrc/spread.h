@@ -35,4 +35,11 @@ struct SpreadPlan {
 // odd one) on stream; measure at the middle slice when measure != 0.
 cudaError_t spread_sweep(const SpreadPlan& p, int parity, int measure, cudaStream_t stream);
 
+// Enqueue the initialisation of every chain from its fields (left stack,
+// right block 0, G at tau = -1, running sign) with the same kernels.
+cudaError_t spread_init(const SpreadPlan& p, cudaStream_t stream);
+
+// Kernel attributes of the spread sequence (once per process, before capture).
+cudaError_t spread_prepare();
+
 }  // namespace pqmc

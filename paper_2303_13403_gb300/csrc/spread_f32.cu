@@ -4,8 +4,8 @@
 
 namespace pqmc {
 
-cudaError_t spread_sweep_f32(const SpreadPlan& p, int parity, int measure, cudaStream_t st) {
-  return spread_sweep_t<float>(p, parity, measure, st);
+cudaError_t spread_sweep_f32(const SpreadPlan& p, int mode, int measure, cudaStream_t st) {
+  return spread_sweep_t<float>(p, mode, measure, st);
 }
 
 }  // namespace pqmc

@@ -11,12 +11,18 @@ __device__ __forceinline__ SpBuf<double> fp64_bufs(const ChainDesc& c, int tsize
 }
 __device__ __forceinline__ int nsig_of(const ChainDesc& c, int s) { return s == 0 ? c.nup : c.ndn; }
 
-// Cholesky factor, diagonal block of panel p (one CTA per spin, chain):
-// right-looking on a shared-memory copy, R_kk = sqrt(pivot), R_kj = C_kj / R_kk,
-// C_ij -= R_ki R_kj inside the block.  Panel 0 first records the Gram
-// diagonal and clears the chain's breakdown flag and log det R.
+// Cholesky factor, diagonal block of panel p (one CTA per spin, chain), on a
+// shared-memory copy: step k takes the pivot C_kk, writes row k of R
+// (R_kj = C_kj / sqrt(C_kk)) and then updates the rows below by
+// C_ij -= R_ki R_kj (one FP64 instruction per element); then R_PP^{-1} by
+// back substitution on the identity, one barrier per row.  Panel 0 first records the Gram diagonal and clears the chain's
+// breakdown flag and log det R.
 __global__ void __launch_bounds__(256) chol_panel_kernel(const ChainDesc* chains, int p, int tsize) {
-  __shared__ double A[kSpPanel][kSpPanel + 1];
+  __shared__ double A[kSpPanel][kSpPanel + 1];    // Schur complements
+  __shared__ double R[kSpPanel][kSpPanel + 1];    // the factor's rows
+  __shared__ double X[1][kSpPanel][kSpPanel + 1]; // inverse, rows in progress
+  __shared__ double Xf[kSpPanel][kSpPanel + 1];   // its final rows
+  __shared__ double ikk[kSpPanel];
   __shared__ int bad;
   const ChainDesc& c = chains[blockIdx.y];
   if (c.st->err) return;
@@ -34,24 +40,34 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(const ChainDesc* chains
       sp.lchol()[s] = 0.0;
     }
   }
-  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) A[e / bw][e % bw] = C[(long)(p0 + e / bw) * ldn + p0 + e % bw];
+  __shared__ double dlim[kSpPanel];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kSpPanel * kSpPanel; e += blockDim.x) {
+    const int i = e / kSpPanel, j = e % kSpPanel;
+    A[i][j] = (i < bw && j < bw) ? C[(long)(p0 + i) * ldn + p0 + j] : 0.0;
+    R[i][j] = 0.0;
+  }
+  if ((int)threadIdx.x < bw) dlim[threadIdx.x] = 1e-12 * d0[p0 + threadIdx.x];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  // upper-triangle pairs (i, j), i <= j, of the trailing block, enumerated so
+  // that every FP64 instruction carries a full warp (the FP64 unit takes as
+  // long for a partial warp)
   for (int k = 0; k < bw; ++k) {
     const double piv = A[k][k];
-    if (!(piv > 1e-12 * d0[p0 + k])) {   // the same value in every thread: uniform exit
+    if (!(piv > dlim[k])) {   // the same value in every thread: uniform exit
       if (threadIdx.x == 0) bad = 1;
       break;
     }
-    const double r = sqrt(piv), ir = 1.0 / r;
-    __syncthreads();
-    for (int j = k + 1 + (int)threadIdx.x; j < bw; j += blockDim.x) A[k][j] *= ir;
-    if (threadIdx.x == 0) A[k][k] = r;
+    const double ir = rsqrt(piv);
+    if ((int)threadIdx.x >= k && (int)threadIdx.x < bw) R[k][threadIdx.x] = threadIdx.x == k ? piv * ir : A[k][threadIdx.x] * ir;
     __syncthreads();
     const int m = bw - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (i <= j) A[i][j] = fma(-A[k][i], A[k][j], A[i][j]);
+    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
+      int i = 0, r = e;
+      while (r >= m - i) { r -= m - i; ++i; }
+      const int ii = k + 1 + i, jj = ii + r;
+      A[ii][jj] = fma(-R[k][ii], R[k][jj], A[ii][jj]);
     }
     __syncthreads();
   }
@@ -62,80 +78,38 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(const ChainDesc* chains
   }
   for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) {
     const int i = e / bw, j = e % bw;
-    if (i <= j) C[(long)(p0 + i) * ldn + p0 + j] = A[i][j];
+    if (i <= j) C[(long)(p0 + i) * ldn + p0 + j] = R[i][j];
   }
-  if (threadIdx.x == 0) {
-    double la = 0.0;
-    for (int k = 0; k < bw; ++k) la += log(A[k][k]);
-    sp.lchol()[s] += la;
+  if (threadIdx.x < 32) {
+    // log det R_PP: one logarithm per lane, summed over the warp
+    double la = (int)threadIdx.x < bw ? log(R[threadIdx.x][threadIdx.x]) : 0.0;
+    la = warp_sum(la);
+    if (threadIdx.x == 0) sp.lchol()[s] += la;
   }
-}
-
-// block row of R: column j >= p1 solves R_PP^T x = C_{P,j} by forward
-// substitution (one thread per column)
-__global__ void __launch_bounds__(128) chol_rows_kernel(const ChainDesc* chains, int p, int tsize) {
-  __shared__ double R[kSpPanel][kSpPanel + 1];
-  __shared__ double ir[kSpPanel];
-  const ChainDesc& c = chains[blockIdx.z];
-  if (c.st->err) return;
-  const int s = blockIdx.y, n = nsig_of(c, s), ldn = c.nmax;
-  const int p0 = p * kSpPanel;
-  if (p0 >= n) return;
-  const int p1 = min(p0 + kSpPanel, n), bw = p1 - p0;
-  if (p1 + (int)(blockIdx.x * blockDim.x) >= n) return;
-  SpBuf<double> sp = fp64_bufs(c, tsize);
-  double* C = sp.c64(s);
-  for (int e = threadIdx.x; e < bw * bw; e += blockDim.x) R[e / bw][e % bw] = C[(long)(p0 + e / bw) * ldn + p0 + e % bw];
-  __syncthreads();
-  if ((int)threadIdx.x < bw) ir[threadIdx.x] = 1.0 / R[threadIdx.x][threadIdx.x];
-  __syncthreads();
-  const int j = p1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double x[kSpPanel];
-#pragma unroll
-  for (int k = 0; k < kSpPanel; ++k) {
-    if (k < bw) {
-      double v = C[(long)(p0 + k) * ldn + j];
-#pragma unroll
-      for (int l = 0; l < kSpPanel; ++l)
-        if (l < k) v = fma(-R[l][k], x[l], v);
-      x[k] = v * ir[k];
-      C[(long)(p0 + k) * ldn + j] = x[k];
-    }
-  }
-}
-
-// inverse of the upper-triangular diagonal block of panel p = blockIdx.x
-// (thread j: column j by back substitution), row-major kSpPanel x kSpPanel
-__global__ void __launch_bounds__(32) tri_inv_kernel(const ChainDesc* chains, int tsize) {
-  __shared__ double R[kSpPanel][kSpPanel + 1];
-  __shared__ double X[kSpPanel][kSpPanel + 1];
-  const ChainDesc& c = chains[blockIdx.z];
-  if (c.st->err) return;
-  const int s = blockIdx.y, n = nsig_of(c, s), ldn = c.nmax;
-  const int p = blockIdx.x, p0 = p * kSpPanel;
-  if (p0 >= n) return;
-  const int bw = min(kSpPanel, n - p0);
-  SpBuf<double> sp = fp64_bufs(c, tsize);
-  const double* C = sp.c64(s);
+  // X = R_PP^{-1} by back substitution on the identity: for k = bw-1 .. 0,
+  // row k of X is final once scaled by 1 / R_kk (kept in Xf), then the rows
+  // i < k take away R_ik times it (one FP64 instruction per element)
   for (int e = threadIdx.x; e < kSpPanel * kSpPanel; e += blockDim.x) {
     const int i = e / kSpPanel, j = e % kSpPanel;
-    R[i][j] = (i < bw && j < bw && i <= j) ? C[(long)(p0 + i) * ldn + p0 + j] : 0.0;
-    X[i][j] = 0.0;
+    X[0][i][j] = (i == j && i < bw) ? 1.0 : 0.0;
+    Xf[i][j] = 0.0;
   }
-  __syncwarp();
-  const int j = threadIdx.x;
-  if (j < bw) {
-    X[j][j] = 1.0 / R[j][j];
-    for (int i = j - 1; i >= 0; --i) {
-      double v = 0.0;
-      for (int k = i + 1; k <= j; ++k) v = fma(R[i][k], X[k][j], v);
-      X[i][j] = -v / R[i][i];
+  if ((int)threadIdx.x < bw) ikk[threadIdx.x] = 1.0 / R[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  for (int k = bw - 1; k >= 0; --k) {
+    if ((int)threadIdx.x < bw) Xf[k][threadIdx.x] = X[0][k][threadIdx.x] * ikk[k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * bw; e += blockDim.x) {
+      const int i = e / bw, j = e % bw;
+      X[0][i][j] = fma(-R[i][k], Xf[k][j], X[0][i][j]);
     }
+    __syncthreads();
   }
-  __syncwarp();
   double* Ri = sp.rinv(s) + (long)p * kSpPanel * kSpPanel;
-  for (int e = threadIdx.x; e < kSpPanel * kSpPanel; e += blockDim.x) Ri[e] = X[e / kSpPanel][e % kSpPanel];
+  for (int e = threadIdx.x; e < kSpPanel * kSpPanel; e += blockDim.x) {
+    const int i = e / kSpPanel, j = e % kSpPanel;
+    Ri[e] = (i < bw && j < bw) ? Xf[i][j] : 0.0;
+  }
 }
 
 // Q = M R^{-1}, one warp per row i of M: panel by panel, t = m_P - q_{<P} R_{<P,P}
@@ -189,30 +163,58 @@ __global__ void __launch_bounds__(256) qform_kernel(const ChainDesc* chains, int
 
 // Gauss-Jordan panel p (columns P = [p0, p1)) of O, one CTA per spin, chain:
 // for each column j of P the largest |O_ij|, i >= j (ties to the lower row),
-// the interchange of rows j and i over all columns, then the elimination of
-// column j restricted to the panel's columns (the rest of the row operations
-// is the block update that follows, from the block row saved at the end)
-__global__ void __launch_bounds__(256) gj_panel_kernel(const ChainDesc* chains, int p, int tsize) {
-  __shared__ double f[kMaxSigma];
-  __shared__ unsigned long long wbest[8];
-  __shared__ int wbi[8];
-  __shared__ int piv;
+// the interchange of rows j and i, then the elimination of column j
+// restricted to the panel's columns (the rest of the row operations is the
+// block update that follows, from the block row saved at the end).  The
+// panel lives in registers: thread t owns column t mod kSpGJ on the rows
+// i = t / kSpGJ + kGJRowStep k, so the elimination is one register DFMA per
+// element.  Column j + 1 is handed on through shared memory by the pass
+// that eliminates column j, together with its pivot candidates; warp 0 picks
+// the pivot and its reciprocal from that column; the owners of the two
+// interchanged rows trade them through shared memory.  Three CTA barriers
+// per step.  The interchanges reach the other columns once, in order, at
+// the end.
+constexpr int kGJThreads = 256;
+constexpr int kGJRowStep = kGJThreads / kSpGJ;
+constexpr int kGJRows = (kMaxSigma + kGJRowStep - 1) / kGJRowStep;   // rows per thread
+static_assert(kGJThreads % kSpGJ == 0 && kSpGJ <= 32, "each thread owns one panel column");
+
+__global__ void __launch_bounds__(kGJThreads) gj_panel_kernel(const ChainDesc* chains, int p, int tsize) {
+  __shared__ double fbuf[2][kMaxSigma];   // column j of the panel before step j (two steps in flight)
+  __shared__ double prow[kSpGJ];          // the pivot row (row i before the interchange)
+  __shared__ double rowj[kSpGJ];          // row j before the interchange
+  __shared__ double ips;
+  __shared__ unsigned long long wbest[kGJThreads / 32];
+  __shared__ int wbi[kGJThreads / 32];
+  __shared__ int piv[kSpGJ];
   const ChainDesc& c = chains[blockIdx.y];
   if (c.st->err) return;
   const int s = blockIdx.x, n = nsig_of(c, s), ldn = c.nmax;
   const int p0 = p * kSpGJ;
   if (p0 >= n) return;
   const int p1 = min(p0 + kSpGJ, n), bw = p1 - p0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = threadIdx.x % kSpGJ, rg = threadIdx.x / kSpGJ;
+  const bool active = col < bw;
   SpBuf<double> sp = fp64_bufs(c, tsize);
   double* A = sp.o64(s);
-  for (int j = p0; j < p1; ++j) {
-    unsigned long long best = 0;
-    int bi = j;
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-      const unsigned long long v = (unsigned long long)__double_as_longlong(A[(long)i * ldn + j]) & 0x7fffffffffffffffull;
-      if (v > best) { best = v; bi = i; }
+  double r[kGJRows];
+  unsigned long long best = 0;
+  int bi = p0;
+#pragma unroll
+  for (int k = 0; k < kGJRows; ++k) {
+    const int i = rg + kGJRowStep * k;
+    r[k] = (active && i < n) ? A[(long)i * ldn + p0 + col] : 0.0;
+    if (active && i < n && col == 0) {
+      fbuf[0][i] = r[k];
+      const unsigned long long av = (unsigned long long)__double_as_longlong(r[k]) & 0x7fffffffffffffffull;
+      if (i >= p0 && av > best) { best = av; bi = i; }
     }
+  }
+  for (int jj = 0; jj < bw; ++jj) {
+    const int j = p0 + jj;
+    double* f = fbuf[jj & 1];
+    double* fnext = fbuf[(jj + 1) & 1];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -221,46 +223,106 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const ChainDesc* chains, 
     }
     if (lane == 0) { wbest[warp] = best; wbi[warp] = bi; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long bb = wbest[0];
-      int ii = wbi[0];
-      for (int u = 1; u < nw; ++u)
-        if (wbest[u] > bb || (wbest[u] == bb && wbi[u] < ii)) { bb = wbest[u]; ii = wbi[u]; }
-      piv = ii;
-      sp.perm(s)[j] = ii;
-    }
-    __syncthreads();
-    const int r = piv;
-    if (r != j)
-      for (int col = threadIdx.x; col < n; col += blockDim.x) {
-        const double t = A[(long)j * ldn + col];
-        A[(long)j * ldn + col] = A[(long)r * ldn + col];
-        A[(long)r * ldn + col] = t;
+    if (threadIdx.x < 32) {
+      // warp 0: the pivot row, its reciprocal from the handed-on column, the
+      // interchange of that column's two entries
+      unsigned long long bb = 0;
+      int ii = j;
+      if (lane < kGJThreads / 32) { bb = wbest[lane]; ii = wbi[lane]; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bb, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ii, o);
+        if (ob > bb || (ob == bb && oi < ii)) { bb = ob; ii = oi; }
       }
-    __syncthreads();
-    const double pv = A[(long)j * ldn + j];
-    const double ip = pv != 0.0 ? 1.0 / pv : 0.0;
-    if (threadIdx.x == 0) {
-      sp.pval(s)[j] = pv;
-      if (pv == 0.0) sp.bad()[s] = 1;
-    }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = A[(long)i * ldn + j];
-    __syncthreads();
-    for (int col = p0 + threadIdx.x; col < p1; col += blockDim.x)
-      A[(long)j * ldn + col] = col == j ? ip : A[(long)j * ldn + col] * ip;
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * bw; e += blockDim.x) {
-      const int i = e / bw, col = p0 + e % bw;
-      if (i == j) continue;
-      const double add = col == j ? 0.0 : A[(long)i * ldn + col];
-      A[(long)i * ldn + col] = fma(-f[i], A[(long)j * ldn + col], add);
+      if (lane == 0) {
+        const double pv = f[ii];
+        ips = pv != 0.0 ? 1.0 / pv : 0.0;
+        piv[jj] = ii;
+        f[ii] = f[j];
+        f[j] = pv;
+        sp.perm(s)[j] = ii;
+        sp.pval(s)[j] = pv;
+        if (pv == 0.0) sp.bad()[s] = 1;
+      }
     }
     __syncthreads();
+    const int ii = piv[jj];
+    // the owners of rows j and ii publish them
+#pragma unroll
+    for (int k = 0; k < kGJRows; ++k) {
+      const int i = rg + kGJRowStep * k;
+      if (active && i == ii) prow[col] = r[k];
+      if (active && i == j) rowj[col] = r[k];
+    }
+    __syncthreads();
+    const double ip = ips;
+    const bool pc = col == jj;
+    const double x = pc ? ip : prow[col] * ip;
+    const double rj = rowj[col];
+    best = 0;
+    bi = j + 1;
+    // eliminate column j: row j becomes the scaled pivot row, row ii takes
+    // the old row j, every other row i loses f_i times the scaled pivot row
+#pragma unroll
+    for (int k = 0; k < kGJRows; ++k) {
+      const int i = rg + kGJRowStep * k;
+      if (active && i < n) {
+        double v = i == ii && ii != j ? rj : r[k];
+        v = i == j ? x : fma(-f[i], x, pc ? 0.0 : v);
+        r[k] = v;
+        if (col == jj + 1) {
+          fnext[i] = v;
+          const unsigned long long av = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+          if (i > j && av > best) { best = av; bi = i; }
+        }
+      }
+    }
   }
+  __syncthreads();
+  // the panel back
+#pragma unroll
+  for (int k = 0; k < kGJRows; ++k) {
+    const int i = rg + kGJRowStep * k;
+    if (active && i < n) A[(long)i * ldn + p0 + col] = r[k];
+  }
+  // the panel back; the other columns take the panel's interchanges composed
+  // into one permutation of at most 2 bw rows (new row rows[e] = old row
+  // src[e]), read once and written once, and the block row of the update
+  __shared__ int rows[2 * kSpGJ], src[2 * kSpGJ], nrows;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int jj = 0; jj < bw; ++jj) { rows[m] = p0 + jj; src[m] = p0 + jj; ++m; }
+    for (int jj = 0; jj < bw; ++jj) {
+      const int j = p0 + jj, r = piv[jj];
+      if (r == j) continue;
+      int ej = -1, er = -1;
+      for (int e = 0; e < m; ++e) {
+        if (rows[e] == j) ej = e;
+        if (rows[e] == r) er = e;
+      }
+      if (er < 0) { rows[m] = r; src[m] = r; er = m++; }
+      const int t = src[ej];
+      src[ej] = src[er];
+      src[er] = t;
+    }
+    nrows = m;
+  }
+  __syncthreads();
+  const int m = nrows;
   double* Tb = sp.tgj(s);
-  for (int e = threadIdx.x; e < bw * n; e += blockDim.x) {
-    const int l = e / n, col = e % n;
-    Tb[(long)l * ldn + col] = A[(long)(p0 + l) * ldn + col];
+  for (int col = threadIdx.x; col < n; col += blockDim.x) {
+    if (col >= p0 && col < p1) continue;
+    double v[2 * kSpGJ];
+#pragma unroll
+    for (int e = 0; e < 2 * kSpGJ; ++e)
+      if (e < m) v[e] = A[(long)src[e] * ldn + col];
+#pragma unroll
+    for (int e = 0; e < 2 * kSpGJ; ++e)
+      if (e < m) {
+        A[(long)rows[e] * ldn + col] = v[e];
+        if (e < bw) Tb[(long)e * ldn + col] = v[e];   // rows[e] = p0 + e for e < bw
+      }
   }
 }
 
@@ -296,33 +358,27 @@ cudaError_t sp_chol_panel(const ChainDesc* d, int nc, int nmax, int p, int tsize
   return cudaGetLastError();
 }
 
-cudaError_t sp_chol_rows(const ChainDesc* d, int nc, int nmax, int p, int tsize, cudaStream_t st) {
-  const int rest = nmax - std::min(nmax, (p + 1) * kSpPanel);
-  if (rest <= 0) return cudaSuccess;
-  chol_rows_kernel<<<dim3((rest + 127) / 128, 2, nc), 128, 0, st>>>(d, p, tsize);
-  return cudaGetLastError();
-}
-
 cudaError_t sp_qform(const ChainDesc* d, int nc, int N, int nmax, int left, int b, int tsize, cudaStream_t st) {
-  tri_inv_kernel<<<dim3((nmax + kSpPanel - 1) / kSpPanel, 2, nc), 32, 0, st>>>(d, tsize);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  (void)nmax;
   qform_kernel<<<dim3((N + 7) / 8, 2, nc), 256, 0, st>>>(d, left, b, tsize);
   return cudaGetLastError();
 }
 
-cudaError_t sp_gj_panel(const ChainDesc* d, int nc, int p, int tsize, cudaStream_t st) {
-  gj_panel_kernel<<<dim3(2, nc), 256, 0, st>>>(d, p, tsize);
+cudaError_t sp_gj_panel(const ChainDesc* d, int nc, int nmax, int p, int tsize, cudaStream_t st) {
+  (void)nmax;
+  gj_panel_kernel<<<dim3(2, nc), kGJThreads, 0, st>>>(d, p, tsize);
   return cudaGetLastError();
 }
+
+cudaError_t spread_prepare() { return cudaSuccess; }
 
 cudaError_t sp_gj_unswap(const ChainDesc* d, int nc, int nmax, int tsize, cudaStream_t st) {
   gj_unswap_kernel<<<dim3((nmax + 127) / 128, 2, nc), 128, 0, st>>>(d, tsize);
   return cudaGetLastError();
 }
 
-cudaError_t spread_sweep_f64(const SpreadPlan& p, int parity, int measure, cudaStream_t st) {
-  return spread_sweep_t<double>(p, parity, measure, st);
+cudaError_t spread_sweep_f64(const SpreadPlan& p, int mode, int measure, cudaStream_t st) {
+  return spread_sweep_t<double>(p, mode, measure, st);
 }
 
 }  // namespace pqmc

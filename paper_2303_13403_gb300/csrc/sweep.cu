@@ -64,10 +64,13 @@ cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains
 }
 
 // chains swept by grid-wide kernel sequences (spread_f64.cu, spread_f32.cu)
-cudaError_t spread_sweep_f64(const SpreadPlan& p, int parity, int measure, cudaStream_t st);
-cudaError_t spread_sweep_f32(const SpreadPlan& p, int parity, int measure, cudaStream_t st);
+cudaError_t spread_sweep_f64(const SpreadPlan& p, int mode, int measure, cudaStream_t st);
+cudaError_t spread_sweep_f32(const SpreadPlan& p, int mode, int measure, cudaStream_t st);
 cudaError_t spread_sweep(const SpreadPlan& p, int parity, int measure, cudaStream_t st) {
-  return p.prec == PQMC_FP64 ? spread_sweep_f64(p, parity, measure, st) : spread_sweep_f32(p, parity, measure, st);
+  return p.prec == PQMC_FP64 ? spread_sweep_f64(p, parity & 1, measure, st) : spread_sweep_f32(p, parity & 1, measure, st);
+}
+cudaError_t spread_init(const SpreadPlan& p, cudaStream_t st) {
+  return p.prec == PQMC_FP64 ? spread_sweep_f64(p, 2, 0, st) : spread_sweep_f32(p, 2, 0, st);
 }
 
 // --------------------------------------------------------------------------

@@ -2,7 +2,7 @@
 autotuning): the 72-site Gutzwiller PQMC batch of the throughput bench, or
 another size, run for a few sweeps with a chosen launch shape.
 
-  python -m paper_2303_13403_gb300.profile_run [--chains 304] [--prec fp32] [--L 6]
+  python -m paper_2303_13403_gb300.profile_run [--chains 304] [--prec fp32] [--L 6] [--spread 1]
          [--two-theta 8] [--n-stab 2] [--delay-k 32] [--cta-threads 256] [--sweeps 2]
 
 Prints one JSON line: milliseconds per sweep (CUDA events on the context's
@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--gemm", type=int, nargs=3, default=None, metavar=("M", "N", "K"))
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--spread", type=int, default=0, help="1: grid-wide kernel sequence per sweep")
+    ap.add_argument("--warmup", type=int, default=-1, help="untimed sweeps first (default 1, spread 2)")
     a = ap.parse_args()
     import torch
     from . import pqmc, workloads
@@ -61,15 +62,21 @@ def main():
     ctx = pqmc.Context([spec] * a.chains, prec=prec, seed=1, n_stab=n_stab, delay_k=a.delay_k,
                        cta_threads=a.cta_threads, stream=stream.cuda_stream, spread=a.spread)
     # warm-up (a spread context captures one graph per sweep direction)
-    ctx.sweep(2 if a.spread else 1, measure=False)
+    warm = a.warmup if a.warmup >= 0 else (2 if a.spread else 1)
+    if warm:
+        ctx.sweep(warm, measure=False)
     ctx.synchronize()
+    c0 = ctx.phase_cycles(0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.sweeps):
         ctx.sweep(1, measure=True)
     e1.record(stream)
     e1.synchronize()
+    c1 = ctx.phase_cycles(0)
+    mcyc = {k: round((c1[k] - c0[k]) / a.sweeps / 1e6, 2) for k in c1 if c1[k] != c0[k]}
     print(json.dumps({"ms_per_sweep": e0.elapsed_time(e1) / a.sweeps, "chains": a.chains, "sites": spec.n_sites,
+                      "mcycles_per_sweep_chain0": mcyc,
                       "precision": a.prec, "n_stab": n_stab, "spread": a.spread, "launch": ctx.launch(),
                       "max_dG": ctx.measure(-1)["max_dG"]}))
     ctx.close()

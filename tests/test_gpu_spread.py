@@ -119,6 +119,24 @@ def test_spread_equals_one_cta_path_fp64():
     b.close()
 
 
+def test_spread_init_matches_one_cta_init_fp64():
+    """The spread initialisation (left stack, right block 0, G at tau = -1)
+    gives the one-CTA initialisation's G to 1e-10 and the oracle's definition
+    of G at tau = -1 on the initial fields."""
+    spec = gutz(9, 4.0)
+    a = pqmc.Context([spec], prec=pqmc.FP64, seed=17, n_stab=2, spread=1)
+    b = pqmc.Context([spec], prec=pqmc.FP64, seed=17, n_stab=2, cta_threads=256)
+    model = opq.Model(oracle_params(spec, n_stab=2))
+    f = a.fields(0)
+    assert np.array_equal(f, b.fields(0))
+    for s, sg in ((0, 1), (1, -1)):
+        Gd = opq.green_definition(model, f, -1, sg)
+        for ctx in (a, b):
+            assert np.abs(ctx.green(0, s) - Gd).max() / np.abs(Gd).max() < 1e-10
+    a.close()
+    b.close()
+
+
 def test_spread_batch_equals_single_chains():
     """Three chains of one shape in one spread context give the chains run
     alone, bit for bit (FP32)."""
