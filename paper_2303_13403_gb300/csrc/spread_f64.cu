@@ -166,23 +166,22 @@ __global__ void __launch_bounds__(256) qform_kernel(const ChainDesc* chains, int
 // the interchange of rows j and i, then the elimination of column j
 // restricted to the panel's columns (the rest of the row operations is the
 // block update that follows, from the block row saved at the end).  The
-// panel lives in registers: thread t owns column t mod kSpGJ on the rows
-// i = t / kSpGJ + kGJRowStep k, so the elimination is one register DFMA per
-// element.  Column j + 1 is handed on through shared memory by the pass
-// that eliminates column j, together with its pivot candidates; warp 0 picks
-// the pivot and its reciprocal from that column; the owners of the two
-// interchanged rows trade them through shared memory.  Three CTA barriers
-// per step.  The interchanges reach the other columns once, in order, at
-// the end.
+// panel stays in shared memory for all its steps, each thread owning one
+// panel column on every 16th row (one FP64 FMA per eliminated element); the
+// pass that eliminates column j also hands on column j + 1 and its pivot
+// candidates, so a step takes two CTA barriers.  The interchanges reach the
+// other columns once, in order, at the end.
+constexpr int kGJLd = kSpGJ + 1;
 constexpr int kGJThreads = 256;
 constexpr int kGJRowStep = kGJThreads / kSpGJ;
-constexpr int kGJRows = (kMaxSigma + kGJRowStep - 1) / kGJRowStep;   // rows per thread
 static_assert(kGJThreads % kSpGJ == 0 && kSpGJ <= 32, "each thread owns one panel column");
+size_t gj_panel_smem(int nmax) { return (size_t)nmax * kGJLd * 8; }
 
 __global__ void __launch_bounds__(kGJThreads) gj_panel_kernel(const ChainDesc* chains, int p, int tsize) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double (*Ap)[kGJLd] = reinterpret_cast<double (*)[kGJLd]>(smem_raw);   // n x bw panel
   __shared__ double fbuf[2][kMaxSigma];   // column j of the panel before step j (two steps in flight)
-  __shared__ double prow[kSpGJ];          // the pivot row (row i before the interchange)
-  __shared__ double rowj[kSpGJ];          // row j before the interchange
+  __shared__ double prow[kSpGJ];          // pivot row of the step, after the interchange
   __shared__ double ips;
   __shared__ unsigned long long wbest[kGJThreads / 32];
   __shared__ int wbi[kGJThreads / 32];
@@ -194,27 +193,28 @@ __global__ void __launch_bounds__(kGJThreads) gj_panel_kernel(const ChainDesc* c
   if (p0 >= n) return;
   const int p1 = min(p0 + kSpGJ, n), bw = p1 - p0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = threadIdx.x % kSpGJ, rg = threadIdx.x / kSpGJ;
-  const bool active = col < bw;
+  const int col = threadIdx.x % kSpGJ, row0 = threadIdx.x / kSpGJ;
   SpBuf<double> sp = fp64_bufs(c, tsize);
   double* A = sp.o64(s);
-  double r[kGJRows];
+  // load; the owners of column 0 hand it on with its pivot candidates
   unsigned long long best = 0;
   int bi = p0;
-#pragma unroll
-  for (int k = 0; k < kGJRows; ++k) {
-    const int i = rg + kGJRowStep * k;
-    r[k] = (active && i < n) ? A[(long)i * ldn + p0 + col] : 0.0;
-    if (active && i < n && col == 0) {
-      fbuf[0][i] = r[k];
-      const unsigned long long av = (unsigned long long)__double_as_longlong(r[k]) & 0x7fffffffffffffffull;
-      if (i >= p0 && av > best) { best = av; bi = i; }
+  for (int i = row0; i < n; i += kGJRowStep) {
+    if (col < bw) {
+      const double v = A[(long)i * ldn + p0 + col];
+      Ap[i][col] = v;
+      if (col == 0) {
+        fbuf[0][i] = v;
+        const unsigned long long av = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+        if (i >= p0 && av > best) { best = av; bi = i; }
+      }
     }
   }
   for (int jj = 0; jj < bw; ++jj) {
     const int j = p0 + jj;
     double* f = fbuf[jj & 1];
     double* fnext = fbuf[(jj + 1) & 1];
+    // candidates of column j: per warp, then warp 0 over the warps
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -224,8 +224,6 @@ __global__ void __launch_bounds__(kGJThreads) gj_panel_kernel(const ChainDesc* c
     if (lane == 0) { wbest[warp] = best; wbi[warp] = bi; }
     __syncthreads();
     if (threadIdx.x < 32) {
-      // warp 0: the pivot row, its reciprocal from the handed-on column, the
-      // interchange of that column's two entries
       unsigned long long bb = 0;
       int ii = j;
       if (lane < kGJThreads / 32) { bb = wbest[lane]; ii = wbi[lane]; }
@@ -235,42 +233,43 @@ __global__ void __launch_bounds__(kGJThreads) gj_panel_kernel(const ChainDesc* c
         const int oi = __shfl_xor_sync(0xffffffffu, ii, o);
         if (ob > bb || (ob == bb && oi < ii)) { bb = ob; ii = oi; }
       }
+      if (ii != j) {
+        if (lane < bw) {
+          const double t = Ap[j][lane];
+          Ap[j][lane] = Ap[ii][lane];
+          Ap[ii][lane] = t;
+        }
+        if (lane == 0) {
+          const double t = f[j];
+          f[j] = f[ii];
+          f[ii] = t;
+        }
+      }
+      __syncwarp();
+      if (lane < bw) prow[lane] = Ap[j][lane];
       if (lane == 0) {
-        const double pv = f[ii];
+        const double pv = Ap[j][jj];
         ips = pv != 0.0 ? 1.0 / pv : 0.0;
         piv[jj] = ii;
-        f[ii] = f[j];
-        f[j] = pv;
         sp.perm(s)[j] = ii;
         sp.pval(s)[j] = pv;
         if (pv == 0.0) sp.bad()[s] = 1;
       }
     }
     __syncthreads();
-    const int ii = piv[jj];
-    // the owners of rows j and ii publish them
-#pragma unroll
-    for (int k = 0; k < kGJRows; ++k) {
-      const int i = rg + kGJRowStep * k;
-      if (active && i == ii) prow[col] = r[k];
-      if (active && i == j) rowj[col] = r[k];
-    }
-    __syncthreads();
+    // eliminate column j from the panel; the owners of column j + 1 hand it on
     const double ip = ips;
-    const bool pc = col == jj;
-    const double x = pc ? ip : prow[col] * ip;
-    const double rj = rowj[col];
     best = 0;
     bi = j + 1;
-    // eliminate column j: row j becomes the scaled pivot row, row ii takes
-    // the old row j, every other row i loses f_i times the scaled pivot row
-#pragma unroll
-    for (int k = 0; k < kGJRows; ++k) {
-      const int i = rg + kGJRowStep * k;
-      if (active && i < n) {
-        double v = i == ii && ii != j ? rj : r[k];
-        v = i == j ? x : fma(-f[i], x, pc ? 0.0 : v);
-        r[k] = v;
+    if (col < bw) {
+      // one FP64 instruction per element: v = add - f_i x with (x, add) =
+      // (1 / pivot, 0) on the pivot column, (pivot row / pivot, O_ic) elsewhere
+      const bool pc = col == jj;
+      const double x = pc ? ip : prow[col] * ip;
+      for (int i = row0; i < n; i += kGJRowStep) {
+        const double add = pc ? 0.0 : Ap[i][col];
+        const double v = i == j ? x : fma(-f[i], x, add);
+        Ap[i][col] = v;
         if (col == jj + 1) {
           fnext[i] = v;
           const unsigned long long av = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
@@ -280,12 +279,7 @@ __global__ void __launch_bounds__(kGJThreads) gj_panel_kernel(const ChainDesc* c
     }
   }
   __syncthreads();
-  // the panel back
-#pragma unroll
-  for (int k = 0; k < kGJRows; ++k) {
-    const int i = rg + kGJRowStep * k;
-    if (active && i < n) A[(long)i * ldn + p0 + col] = r[k];
-  }
+  for (int e = threadIdx.x; e < n * bw; e += blockDim.x) A[(long)(e / bw) * ldn + p0 + e % bw] = Ap[e / bw][e % bw];
   // the panel back; the other columns take the panel's interchanges composed
   // into one permutation of at most 2 bw rows (new row rows[e] = old row
   // src[e]), read once and written once, and the block row of the update
@@ -365,12 +359,14 @@ cudaError_t sp_qform(const ChainDesc* d, int nc, int N, int nmax, int left, int 
 }
 
 cudaError_t sp_gj_panel(const ChainDesc* d, int nc, int nmax, int p, int tsize, cudaStream_t st) {
-  (void)nmax;
-  gj_panel_kernel<<<dim3(2, nc), kGJThreads, 0, st>>>(d, p, tsize);
+  gj_panel_kernel<<<dim3(2, nc), kGJThreads, gj_panel_smem(nmax), st>>>(d, p, tsize);
   return cudaGetLastError();
 }
 
-cudaError_t spread_prepare() { return cudaSuccess; }
+cudaError_t spread_prepare() {
+  return cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gj_panel_smem(kMaxSigma));
+}
 
 cudaError_t sp_gj_unswap(const ChainDesc* d, int nc, int nmax, int tsize, cudaStream_t st) {
   gj_unswap_kernel<<<dim3((nmax + 127) / 128, 2, nc), 128, 0, st>>>(d, tsize);
