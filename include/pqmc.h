@@ -449,12 +449,12 @@ pqmc_status pqmc_inject_error(pqmc_ctx* ctx, int chain, int code);
  * the library holds until the process exits.  A chain needing more than
  * 16 MiB (roughly N > 128 at Ltau = 200, n_stab = 10) is rejected with
  * PQMC_EINVAL.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (each call
- * re-initialises what it reads), so calls that overlap on the GPU, from any
- * stream or thread, race: serialise them.  The call synchronises `stream`
- * before it returns and reports PQMC_ESTAB / PQMC_ENAN / PQMC_ECUDA like the
- * other entry points (message: pqmc_last_error(NULL)). */
+ * (cudaGetSymbolAddress).  All calls share the array and it keeps the last
+ * call's contents (each call re-initialises what it reads), so calls that
+ * overlap on the GPU, from any stream or thread, race: serialise them.  The
+ * call synchronises `stream` before it returns and reports PQMC_ESTAB /
+ * PQMC_ENAN / PQMC_ECUDA like the other entry points (message:
+ * pqmc_last_error(NULL)). */
 pqmc_status pqmc_green_noalloc(const pqmc_chain_spec* spec, int n_stab, const int8_t* d_fields,
                                double* d_G, double* d_logw, void* stream);
 
