@@ -281,6 +281,16 @@ pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len);
  * out[0..3] = (logabs_up, sign_up, logabs_dn, sign_dn). */
 pqmc_status pqmc_get_weight(pqmc_ctx* ctx, int chain, double* out);
 
+/* Run log (no counterpart in the paper: bookkeeping of a run).  Appends one
+ * JSON line per chain to the text file at `path`: chain and Philox chain
+ * index, sites, slices, precision, sweeps done, records, the sign-reweighted
+ * means of the chain's records (E/site, docc, S_AFM), the mean weight sign,
+ * the acceptance, max |G - G_fresh| and the latest stabilisation's value,
+ * stabilisations done, log|det| and sign of each spin's weight at the last
+ * stabilisation, the running sign, and the chain's error bits.  Synchronises
+ * the context's stream; PQMC_EINVAL when the file cannot be written. */
+pqmc_status pqmc_write_run_log(pqmc_ctx* ctx, const char* path);
+
 /* Accept bits (0/1) of the first n proposals of a chain in visiting order
  * (requires opts.accept_log >= n). */
 pqmc_status pqmc_get_accept_log(pqmc_ctx* ctx, int chain, uint8_t* out, long n);

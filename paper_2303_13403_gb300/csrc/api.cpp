@@ -1259,6 +1259,59 @@ pqmc_status pqmc_restore(pqmc_ctx* ctx, const void* buf, size_t len) {
   return PQMC_OK;
 }
 
+pqmc_status pqmc_write_run_log(pqmc_ctx* ctx, const char* path) {
+  NvtxRange range("pqmc_write_run_log");
+  if (!ctx || !path) return PQMC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  std::ofstream f(path, std::ios::app);
+  if (!f) return fail(ctx, PQMC_EINVAL, std::string("cannot open ") + path);
+  f.precision(17);
+  const char* prec[] = {"fp64", "fp32", "bf16x3"};
+  for (int c = 0; c < (int)ctx->chains.size(); ++c) {
+    std::vector<double> rec;
+    int n = 0;
+    pqmc_status s = read_records(ctx, c, rec, n);
+    if (s != PQMC_OK) return s;
+    ChainState st;
+    if ((s = read_state(ctx, c, st)) != PQMC_OK) return s;
+    const HostChain& h = ctx->chains[c];
+    // sign-reweighted means over the chain's records
+    double ts = 0, tE = 0, tD = 0, tS = 0;
+    for (int m = 0; m < n; ++m) {
+      const double sg = rec[(size_t)m * kRecord + 0];
+      ts += sg;
+      tE += sg * rec[(size_t)m * kRecord + 1];
+      tD += sg * rec[(size_t)m * kRecord + 2];
+      tS += sg * rec[(size_t)m * kRecord + 5];
+    }
+    auto num = [&](double v) {
+      std::ostringstream o;
+      o.precision(17);
+      if (std::isfinite(v)) o << v; else o << "null";
+      return o.str();
+    };
+    const int nd = std::min(st.n_dG, kDGHistory);
+    double dG_last = NAN;
+    if (nd > 0) {
+      double v = 0;
+      cudaMemcpy(&v, ctx->desc[c].dG + (st.n_dG - 1) % kDGHistory, sizeof v, cudaMemcpyDeviceToHost);
+      dG_last = v;
+    }
+    f << "{\"chain\": " << c << ", \"chain_index\": " << ctx->desc[c].chain_index << ", \"sites\": " << h.N
+      << ", \"slices\": " << h.Ltau + 2 << ", \"precision\": \"" << prec[ctx->prec] << "\", \"sweeps\": "
+      << ctx->sweep_index << ", \"records\": " << n << ", \"E_per_site\": " << num(ts != 0 ? tE / ts : NAN)
+      << ", \"docc\": " << num(ts != 0 ? tD / ts : NAN) << ", \"s_afm\": " << num(ts != 0 ? tS / ts : NAN)
+      << ", \"sign\": " << num(n ? ts / n : NAN) << ", \"accept\": "
+      << num(st.n_prop ? (double)st.n_acc / st.n_prop : NAN) << ", \"max_dG\": " << num(st.max_dG)
+      << ", \"dG_last\": " << num(dG_last) << ", \"stabilisations\": " << st.n_dG << ", \"logw\": ["
+      << num(st.logw[0][0]) << ", " << num(st.logw[1][0]) << "], \"weight_sign\": [" << num(st.logw[0][1])
+      << ", " << num(st.logw[1][1]) << "], \"running_sign\": " << num(st.sign_running)
+      << ", \"error\": " << st.err << "}\n";
+  }
+  return f ? PQMC_OK : fail(ctx, PQMC_EINVAL, std::string("write failed: ") + path);
+}
+
 pqmc_status pqmc_get_weight(pqmc_ctx* ctx, int chain, double* out) {
   if (!chain_ok(ctx, chain) || !out) return PQMC_EINVAL;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);

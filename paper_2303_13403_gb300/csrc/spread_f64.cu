@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) qform_kernel(const ChainDesc* chains, int
 // candidates, so a step takes two CTA barriers.  The interchanges reach the
 // other columns once, in order, at the end.
 constexpr int kGJLd = kSpGJ + 1;
-constexpr int kGJThreads = 256;
+constexpr int kGJThreads = 512;
 constexpr int kGJRowStep = kGJThreads / kSpGJ;
 static_assert(kGJThreads % kSpGJ == 0 && kSpGJ <= 32, "each thread owns one panel column");
 size_t gj_panel_smem(int nmax) { return (size_t)nmax * kGJLd * 8; }

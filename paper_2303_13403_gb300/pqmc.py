@@ -86,6 +86,7 @@ SIGNATURES = [
     ("pqmc_checkpoint", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     ("pqmc_restore", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("pqmc_get_weight", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    ("pqmc_write_run_log", C.c_int, [C.c_void_p, C.c_char_p]),
     ("pqmc_get_accept_log", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint8), C.c_long]),
     ("pqmc_get_stab_errors", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     ("pqmc_get_phase_cycles", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong)]),
@@ -283,6 +284,10 @@ class Context:
         out = (C.c_longlong * 16)()
         _check(load().pqmc_get_phase_cycles(self._h, chain, out), self._h)
         return dict(zip(self.PHASES, list(out)))
+
+    def write_run_log(self, path):
+        """pqmc_write_run_log: append one JSON line per chain to `path`."""
+        _check(load().pqmc_write_run_log(self._h, str(path).encode()), self._h)
 
     def launch_count(self):
         return int(load().pqmc_launch_count(self._h))
