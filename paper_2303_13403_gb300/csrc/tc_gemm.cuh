@@ -5,7 +5,7 @@
 // C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 in tensor memory
 // (the same split as the mma.sync path; Henry, Tang & Heinecke 2019).
 //
-// One CTA computes the whole product in tiles of 128 rows x up to 256
+// One CTA computes the whole product in tiles of 128 rows x up to 192
 // columns: the threads split a 128 x 64 slice of A and a 64-deep slice of B
 // into BF16 hi/lo tiles in shared memory (canonical K-major layout without
 // swizzle: 8 x 8 core matrices, 128 B each), one thread issues the
@@ -26,7 +26,9 @@
 namespace pqmc {
 
 constexpr int kTcM = 128;                 // rows per tile (the MMA's M)
-constexpr int kTcN = 256;                 // largest tile width (the MMA's N, multiple of 16)
+constexpr int kTcN = 192;                 // largest tile width (the MMA's N, multiple of 16); 192 keeps
+                                          // the staging area within a 100 KB shared-memory carve-out
+                                          // (more L1 for the chain's global-memory G and scratch)
 constexpr int kTcK = 64;                  // depth of one staged slice (four 16-deep MMA steps)
 constexpr int kTcCols = 256;              // TMEM columns held by the CTA
 constexpr uint32_t kTcTileA = kTcM * kTcK * 2;          // bytes of one BF16 A tile
@@ -35,7 +37,7 @@ constexpr uint32_t kTcOffAlo = kTcTileA;
 constexpr uint32_t kTcOffBhi = 2 * kTcTileA;
 constexpr uint32_t kTcOffBlo = 2 * kTcTileA + kTcTileB;
 constexpr uint32_t kTcOffBar = 2 * kTcTileA + 2 * kTcTileB;   // mbarrier (8 B), TMEM address (4 B), phase (4 B)
-constexpr uint32_t kTcBytes = kTcOffBar + 64;                  // staging area of one CTA (96 KB + 64 B)
+constexpr uint32_t kTcBytes = kTcOffBar + 64;                  // staging area of one CTA (80 KB + 64 B)
 constexpr int kTcSpinLimit = 1 << 22;
 
 // byte offset of element (r, k) of a K-major tile, k < kTcK: core matrix
