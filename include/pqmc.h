@@ -318,9 +318,13 @@ pqmc_status pqmc_get_dims(pqmc_ctx* ctx, int chain, int* out);
 /* Number of chains in the context, or -1 for NULL. */
 int pqmc_num_chains(const pqmc_ctx* ctx);
 
-/* Bytes of device memory held by the context (uploaded from the host at
- * creation), or 0 for NULL. */
+/* Bytes of device memory held by the context, or 0 for NULL. */
 size_t pqmc_device_bytes(const pqmc_ctx* ctx);
+
+/* Bytes copied from host memory into the context's device memory at
+ * creation (model tables, trial orbitals, initial fields, chain states; the
+ * rest of the arena is cleared on the device), or 0 for NULL. */
+size_t pqmc_upload_bytes(const pqmc_ctx* ctx);
 
 /* Device kernels launched by this context so far (all entry points; a sweep
  * graph replay counts its two kernels). */

@@ -70,7 +70,7 @@ struct pqmc_ctx {
   size_t tsize = 8;
   std::vector<HostChain> chains;
   std::vector<ChainDesc> desc;
-  std::vector<unsigned char> host_arena;   // initial contents of the device arena
+  size_t upload_bytes = 0;                 // bytes copied from host memory into the arena at creation
   unsigned char* d_arena = nullptr;
   size_t arena_bytes = 0;
   ChainDesc* d_desc = nullptr;            // descriptors by chain index (initialisation launches)
@@ -181,16 +181,35 @@ pqmc_status check_spec(const pqmc_chain_spec& s, int n_stab, std::string& why) {
 
 namespace {
 
+// The parts of a new context's arena that do not start at zero, as segments
+// at arena offsets: the arena is cleared on the device and only these are
+// copied from host memory.
+struct Staged {
+  struct Segment {
+    size_t off;
+    std::vector<unsigned char> bytes;
+  };
+  std::vector<Segment> seg;
+  // a zeroed host segment of n bytes for arena offset off
+  unsigned char* at(size_t off, size_t n) {
+    seg.push_back({off, std::vector<unsigned char>(n, 0)});
+    return seg.back().bytes.data();
+  }
+  size_t bytes() const {
+    size_t b = 0;
+    for (const Segment& g : seg) b += g.bytes.size();
+    return b;
+  }
+};
+
 template <typename T>
-void put(std::vector<unsigned char>& a, size_t off, const std::vector<double>& src, int rows, int cols, int ld) {
-  T* p = reinterpret_cast<T*>(a.data() + off);
+void put(Staged& a, size_t off, const std::vector<double>& src, int rows, int cols, int ld) {
+  T* p = reinterpret_cast<T*>(a.at(off, (size_t)rows * ld * sizeof(T)));
   for (int i = 0; i < rows; ++i)
     for (int j = 0; j < cols; ++j) p[(size_t)i * ld + j] = (T)src[(size_t)i * cols + j];
 }
 
-void put_raw(std::vector<unsigned char>& a, size_t off, const void* src, size_t n) {
-  memcpy(a.data() + off, src, n);
-}
+void put_raw(Staged& a, size_t off, const void* src, size_t n) { memcpy(a.at(off, n), src, n); }
 
 pqmc_status sync_check(pqmc_ctx* ctx) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -301,6 +320,10 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   ctx->chains.resize(n);
   struct TrialOut { std::vector<double> P[2]; };
   std::vector<TrialOut> trials(n);
+  // chains with the same lattice, trial parameters and particle numbers share
+  // their trial orbitals: trial_src[c] is the chain whose orbitals c uses
+  std::vector<int> trial_src(n);
+  std::map<std::string, int> trial_first;
   for (int c = 0; c < n; ++c) {
     const pqmc_chain_spec& s = specs[c];
     HostChain& h = ctx->chains[c];
@@ -337,7 +360,12 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     const ModelTables& mt = models[key];
     Lattice lat{is_tv(s) ? (int)PQMC_HONEYCOMB : s.lattice.kind, s.lattice.Lx, s.lattice.Ly, s.lattice.t,
                 s.lattice.tp};
-    for (int sp = 0; sp < (is_tv(s) ? 1 : 2); ++sp) {
+    char tkey[160];
+    snprintf(tkey, sizeof tkey, "|%.17g|%.17g|%d|%d", s.trial.M_N, s.trial.tiebreak, h.nup, h.ndn);
+    const auto tf = trial_first.find(key + tkey);
+    trial_src[c] = tf == trial_first.end() ? c : tf->second;
+    if (tf == trial_first.end()) trial_first[key + tkey] = c;
+    for (int sp = 0; sp < (is_tv(s) ? 1 : 2) && trial_src[c] == c; ++sp) {
       double gap = 0;
       if (!trial_orbitals(lat, mt.K, mt.eps, s.trial.M_N, s.trial.tiebreak, sp == 0 ? 1 : -1,
                           sp == 0 ? h.nup : h.ndn, trials[c].P[sp], gap)) {
@@ -392,9 +420,9 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
   ctx->arena_bytes = off;
 
   // ---- initial arena contents
-  ctx->host_arena.assign(off, 0);
-  auto& A = ctx->host_arena;
+  Staged A;
   std::map<std::string, bool> written;
+  double* last_all = reinterpret_cast<double*>(A.at(ctx->off_last, (size_t)n * kRecord * 8));
   for (int c = 0; c < n; ++c) {
     HostChain& h = ctx->chains[c];
     const pqmc_chain_spec& s = h.spec;
@@ -410,25 +438,26 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
       }
       put<double>(A, h.off_expKm64, mt.expKm, h.N, h.N, h.N);
       put<double>(A, h.off_K64, mt.K, h.N, h.N, h.N);
-      memcpy(A.data() + h.off_eps, mt.eps.data(), (size_t)h.N * 8);
+      put_raw(A, h.off_eps, mt.eps.data(), (size_t)h.N * 8);
       if (is_tv(s)) {
-        memcpy(A.data() + h.off_bonds, mt.bond_ends.data(), mt.bond_ends.size() * 4);
-        memcpy(A.data() + h.off_sbonds, mt.site_bonds.data(), mt.site_bonds.size() * 4);
+        put_raw(A, h.off_bonds, mt.bond_ends.data(), mt.bond_ends.size() * 4);
+        put_raw(A, h.off_sbonds, mt.site_bonds.data(), mt.site_bonds.size() * 4);
       }
       written[key] = true;
     }
     // P_sigma column-major (ld N) in blocks of N x nmax
-    double* P = reinterpret_cast<double*>(A.data() + h.off_P);
+    double* P = reinterpret_cast<double*>(A.at(h.off_P, 2 * (size_t)h.N * h.nmax * 8));
+    const TrialOut& tr = trials[trial_src[c]];
     for (int sp = 0; sp < 2; ++sp) {
       const int ns = sp == 0 ? h.nup : h.ndn;
       for (int i = 0; i < h.N; ++i)
-        for (int k = 0; k < ns; ++k) P[(size_t)sp * h.N * h.nmax + (size_t)k * h.N + i] = trials[c].P[sp][(size_t)i * ns + k];
+        for (int k = 0; k < ns; ++k) P[(size_t)sp * h.N * h.nmax + (size_t)k * h.N + i] = tr.P[sp][(size_t)i * ns + k];
     }
-    int8_t* F = reinterpret_cast<int8_t*>(A.data() + h.off_fields);
+    int8_t* F = reinterpret_cast<int8_t*>(A.at(h.off_fields, (size_t)(h.Ltau + 2) * h.nfld));
     const uint32_t chain_index = (uint32_t)(o.chain_offset + c);
     for (int t = 0; t < h.Ltau + 2; ++t)
       for (int i = 0; i < h.nfld; ++i) F[(size_t)t * h.nfld + i] = (int8_t)initial_field(o.seed, chain_index, t, i);
-    double* last = reinterpret_cast<double*>(A.data() + ctx->off_last) + (size_t)c * kRecord;
+    double* last = last_all + (size_t)c * kRecord;
     for (int k = 0; k < kRecord; ++k) last[k] = NAN;
     ChainState st{};
     st.sign_running = 1.0;
@@ -518,7 +547,14 @@ pqmc_status build_ctx(int n, const pqmc_chain_spec* specs, const pqmc_opts* opts
     }
     ctx->spread = true;
   }
-  e = cudaMemcpyAsync(ctx->d_arena, A.data(), ctx->arena_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  // clear the arena on the device, then copy in the parts that the host set
+  // (model tables, trial orbitals, initial fields, chain states, records);
+  // pqmc_init synchronises before it returns, so A outlives the copies
+  e = cudaMemsetAsync(ctx->d_arena, 0, ctx->arena_bytes, ctx->stream);
+  for (size_t g = 0; g < A.seg.size() && e == cudaSuccess; ++g)
+    e = cudaMemcpyAsync(ctx->d_arena + A.seg[g].off, A.seg[g].bytes.data(), A.seg[g].bytes.size(),
+                        cudaMemcpyHostToDevice, ctx->stream);
+  ctx->upload_bytes = A.bytes();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->d_desc, ctx->desc.data(), sizeof(ChainDesc) * n, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = upload_run_order(ctx);
@@ -1376,6 +1412,7 @@ int pqmc_num_chains(const pqmc_ctx* ctx) { return ctx ? (int)ctx->chains.size() 
 long pqmc_launch_count(const pqmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 size_t pqmc_device_bytes(const pqmc_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
+size_t pqmc_upload_bytes(const pqmc_ctx* ctx) { return ctx ? ctx->upload_bytes : 0; }
 
 const char* pqmc_last_error(const pqmc_ctx* ctx) {
   if (!ctx) return g_init_error.c_str();

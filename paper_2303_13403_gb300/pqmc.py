@@ -94,6 +94,7 @@ SIGNATURES = [
     ("pqmc_num_chains", C.c_int, [C.c_void_p]),
     ("pqmc_launch_count", C.c_long, [C.c_void_p]),
     ("pqmc_device_bytes", C.c_size_t, [C.c_void_p]),
+    ("pqmc_upload_bytes", C.c_size_t, [C.c_void_p]),
     ("pqmc_last_error", C.c_char_p, [C.c_void_p]),
     ("pqmc_free", None, [C.c_void_p]),
     ("pqmc_host_model", C.c_int, [C.POINTER(Lattice), C.c_double, C.POINTER(Trial), C.c_int,
@@ -223,6 +224,9 @@ class Context:
 
     def device_bytes(self):
         return int(load().pqmc_device_bytes(self._h))
+
+    def upload_bytes(self):
+        return int(load().pqmc_upload_bytes(self._h))
 
     def green(self, chain=0, spin=0):
         N = self.dims(chain)["N"]
