@@ -146,6 +146,23 @@ def test_batch_of_uneven_chains_equals_single_chains():
         assert np.array_equal(batch.measurements(c), one.measurements(0))
 
 
+def test_identical_chains_share_trial_orbitals_bit_for_bit():
+    """Chains with one lattice and trial share one host eigensolution; the
+    context uploads only the host-set part of its arena.  A batch of equal
+    specs must still equal the chains run one at a time."""
+    specs = [SMALL] * 3
+    batch = pqmc.Context(specs, prec=pqmc.FP64, seed=4, n_stab=5, accept_log=1 << 16)
+    assert 0 < batch.upload_bytes() < batch.device_bytes()
+    batch.sweep(2)
+    for c in range(3):
+        one = pqmc.Context([SMALL], prec=pqmc.FP64, seed=4, n_stab=5, chain_offset=c, accept_log=1 << 16)
+        one.sweep(2)
+        d = one.dims()
+        n = 2 * (d["Ltau"] + 2) * d["N"]
+        assert np.array_equal(batch.accept_log(n, c), one.accept_log(n))
+        assert np.array_equal(batch.green(c, 1), one.green(0, 1))
+
+
 def test_fp32_stabilisation_error_and_green():
     """FP32 wraps and updates amplify rounding by about cond(B_tau) per slice;
     with a 2-slice stabilisation interval max |G - G_FP64| stays below 1e-4."""
