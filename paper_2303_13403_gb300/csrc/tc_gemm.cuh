@@ -25,7 +25,7 @@
 
 namespace pqmc {
 
-constexpr int kTcM = 128;                 // rows per tile (the MMA's M)
+constexpr int kTcM = 128;                 // rows per tile (the MMA's M; the staging maps rows by & 127)
 constexpr int kTcN = 192;                 // largest tile width (the MMA's N, multiple of 16); 192 keeps
                                           // the staging area within a 100 KB shared-memory carve-out
                                           // (more L1 for the chain's global-memory G and scratch)
@@ -123,13 +123,20 @@ __device__ __forceinline__ bool tc_wait(unsigned char* st) {
   return done != 0;
 }
 
-template <typename TA>
-__device__ __forceinline__ void tc_split_store(unsigned char* hi, unsigned char* lo, uint32_t off, TA v) {
-  const float x = (float)v;
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+// Split eight FP32 values into BF16 hi = bf16(x) and lo = bf16(x - hi) and
+// store each part as one 16-byte row of a core matrix (element q at byte 2q)
+__device__ __forceinline__ void tc_split_store8(unsigned char* hi, unsigned char* lo, uint32_t off, const float v[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
+    h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // C = A B (split BF16, FP32 accumulation); A(i, k) = A[i sai + k sak],
@@ -159,49 +166,40 @@ __device__ void cta_gemm_tc(int M, int Nn, int K, const float* A, int sai, int s
         const int kw = 16 * ks;
         // split the A slice (128 x kw) and the B slice (kw x nt, stored as
         // its transpose, nt x kw) into the hi / lo tiles (zero outside the
-        // operands); consecutive threads walk the operand's unit-stride index
-        // (the loads of a batch of eight elements are issued before its
-        // stores, so that eight loads per thread are in flight at once)
-        constexpr int kB = 8;
-        for (int e0 = tid; e0 < kTcM * kw; e0 += kB * nthr) {
-          float v[kB];
+        // operands).  One item is one 16-byte row of a core matrix: eight
+        // depths 8 kg .. 8 kg + 7 of one row r of A or one column n of B;
+        // consecutive threads take consecutive rows / columns, the operands'
+        // unit-stride index in the wrap (a row-major A is read as two 16-byte
+        // vectors per item instead)
+        const int kgs = kw >> 3;
+        const bool a_vec = sak == 1 && (sai & 3) == 0 && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+        for (int it = tid; it < kTcM * kgs; it += nthr) {
+          const int r = it & (kTcM - 1), kg = it >> 7;
+          const int i = m0 + r, kb = k0 + 8 * kg;
+          float v[8];
+          if (a_vec && i < M && kb + 8 <= K) {
+            const float4 x0 = *reinterpret_cast<const float4*>(A + (long)i * sai + kb);
+            const float4 x1 = *reinterpret_cast<const float4*>(A + (long)i * sai + kb + 4);
+            v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+            v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+          } else {
 #pragma unroll
-          for (int q = 0; q < kB; ++q) {
-            const int e = e0 + q * nthr;
-            int r, k;
-            if (sai == 1) { r = e % kTcM; k = e / kTcM; } else { k = e % kw; r = e / kw; }
-            const int i = m0 + r, kk = k0 + k;
-            v[q] = (e < kTcM * kw && i < M && kk < K) ? A[(long)i * sai + (long)kk * sak] : 0.0f;
+            for (int q = 0; q < 8; ++q)
+              v[q] = (i < M && kb + q < K) ? A[(long)i * sai + (long)(kb + q) * sak] : 0.0f;
           }
-#pragma unroll
-          for (int q = 0; q < kB; ++q) {
-            const int e = e0 + q * nthr;
-            if (e < kTcM * kw) {
-              int r, k;
-              if (sai == 1) { r = e % kTcM; k = e / kTcM; } else { k = e % kw; r = e / kw; }
-              tc_split_store(ahi, alo, tc_off(r, k), v[q]);
-            }
-          }
+          tc_split_store8(ahi, alo, tc_off(r, 8 * kg), v);
         }
-        for (int e0 = tid; e0 < nt * kw; e0 += kB * nthr) {
-          float v[kB];
+        // item -> (kg, n) = divmod(it, nt) by a multiply-high: it < 2^13 and
+        // nt <= kTcN < 2^8, so ceil(2^32 / nt) gives the exact quotient
+        const uint32_t mg = (uint32_t)((0x100000000ull + (uint64_t)nt - 1) / (uint64_t)nt);
+        for (int it = tid; it < nt * kgs; it += nthr) {
+          const int kg = (int)__umulhi((uint32_t)it, mg), n = it - kg * nt;
+          const int j = n0 + n, kb = k0 + 8 * kg;
+          float v[8];
 #pragma unroll
-          for (int q = 0; q < kB; ++q) {
-            const int e = e0 + q * nthr;
-            int n, k;
-            if (sbj == 1) { n = e % nt; k = e / nt; } else { k = e % kw; n = e / kw; }
-            const int j = n0 + n, kk = k0 + k;
-            v[q] = (e < nt * kw && j < Nn && kk < K) ? B[(long)kk * sbk + (long)j * sbj] : 0.0f;
-          }
-#pragma unroll
-          for (int q = 0; q < kB; ++q) {
-            const int e = e0 + q * nthr;
-            if (e < nt * kw) {
-              int n, k;
-              if (sbj == 1) { n = e % nt; k = e / nt; } else { k = e % kw; n = e / kw; }
-              tc_split_store(bhi, blo, tc_off(n, k), v[q]);
-            }
-          }
+          for (int q = 0; q < 8; ++q)
+            v[q] = (j < Nn && kb + q < K) ? B[(long)(kb + q) * sbk + (long)j * sbj] : 0.0f;
+          tc_split_store8(bhi, blo, tc_off(n, 8 * kg), v);
         }
         // the tiles written by the threads (generic proxy) are read by the
         // tensor cores (async proxy)
