@@ -301,8 +301,8 @@ def run_ours(a):
                                          "against": "G rebuilt from the stacks in the path precision"}}
 
     def time_to_sigma(name, n_sweeps):
-        """Wall time to sigma(E/site) = 1e-3, warm-up included (the survey's
-        definition): a fresh context of the bench's chains runs n_sweeps
+        """Wall time to sigma(E/site) = 1e-3, warm-up included (the time a
+        user waits for that error bar from a fresh start): a fresh context of the bench's chains runs n_sweeps
         measured sweeps, each timed with CUDA events on the context's
         stream.  The warm-up length is the shortest of 2, 4, 8, 12, 16 sweeps
         after which the pooled E/site of the first and second halves of the

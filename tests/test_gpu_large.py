@@ -69,7 +69,7 @@ def test_sweeps_against_green_definition(L, two_theta, prec, n_stab, sweeps):
                 err = np.abs(G - Gd).max() / np.abs(Gd).max()
                 assert err < 1e-10, (N, k, s, err)
             else:
-                # FP32: the benchmark spec's bound; BF16X3 (about 16 significant
+                # FP32: the 1e-4 accuracy target; BF16X3 (about 16 significant
                 # bits in its products): an order of magnitude above it
                 err = np.abs(G - Gd).max()
                 assert err < (1e-4 if prec == pqmc.FP32 else 2e-3), (N, k, s, err)
