@@ -199,8 +199,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 # DRAM bytes (read + write) per chain and sweep of the sweep kernel, by
 # (precision, N, Ltau, delayed block, CTA threads), from one ncu capture of
 # that launch shape (profiles/sweep_kernel_gutz72_ncu.md: 304 chains, one
-# sweep, 547.4 + 499.9 MB).
-DRAM_BYTES_PER_CHAIN_SWEEP = {("fp32", 72, 80, 32, 256): (547.371776e6 + 499.914496e6) / 304}
+# sweep, 550.7 + 499.6 MB).
+DRAM_BYTES_PER_CHAIN_SWEEP = {("fp32", 72, 80, 32, 256): (550.736384e6 + 499.562496e6) / 304}
 
 
 def run_ours(a):
