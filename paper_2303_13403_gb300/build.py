@@ -11,8 +11,8 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["sweep.cu", "sweep_f64.cu", "sweep_f32.cu", "sweep_f32_dense.cu", "spread_f64.cu", "spread_f32.cu",
-              "probe.cu"]
+CU_SOURCES = ["sweep.cu", "sweep_f64.cu", "sweep_f32.cu", "sweep_f32_256.cu", "sweep_f32_512.cu",
+              "sweep_f32_dense.cu", "spread_f64.cu", "spread_f32.cu", "probe.cu"]
 CPP_SOURCES = ["api.cpp", "model.cpp"]
 
 

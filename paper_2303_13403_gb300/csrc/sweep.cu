@@ -45,12 +45,16 @@ cudaError_t launch_init(int prec, int tpb, int boost, const ChainDesc* d_chains,
                         size_t res, int* d_err, cudaStream_t stream, int b_at) {
   if (prec == 0) return launch_init_f64(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
   if (boost) return launch_init_f32_dense(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
+  if (tpb == 256) return launch_init_f32_256(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
+  if (tpb == 512) return launch_init_f32_512(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
   return launch_init_f32(tpb, d_chains, chain0, n, seed, res, d_err, stream, b_at);
 }
 
 cudaError_t prepare_sweep(int prec, int tpb, int boost, size_t res) {
   if (prec == 0) return prepare_sweep_f64(tpb, res, 0);
   if (boost) return prepare_sweep_f32_dense(tpb, res, 0);
+  if (tpb == 256) return prepare_sweep_f32_256(tpb, res, tc_launch(prec, tpb));
+  if (tpb == 512) return prepare_sweep_f32_512(tpb, res, tc_launch(prec, tpb));
   return prepare_sweep_f32(tpb, res, tc_launch(prec, tpb));
 }
 
@@ -59,6 +63,12 @@ cudaError_t launch_sweep(int prec, int tpb, int boost, const ChainDesc* d_chains
   if (prec == 0) return launch_sweep_f64(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream, 0);
   if (boost)
     return launch_sweep_f32_dense(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream, 0);
+  if (tpb == 256)
+    return launch_sweep_f32_256(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream,
+                                tc_launch(prec, tpb));
+  if (tpb == 512)
+    return launch_sweep_f32_512(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream,
+                                tc_launch(prec, tpb));
   return launch_sweep_f32(tpb, d_chains, n, seed, sweep_ctr, n_sweeps, measure, res, d_err, stream,
                           tc_launch(prec, tpb));
 }

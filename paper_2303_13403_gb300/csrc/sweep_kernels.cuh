@@ -1953,6 +1953,8 @@ static cudaError_t launch_sweep_t(const ChainDesc* d_chains, int n, uint64_t see
                                int n_sweeps, int measure, size_t res, int* d_err, cudaStream_t stream, int tc_on);
 PQMC_DECLARE_LAUNCHERS(f64)
 PQMC_DECLARE_LAUNCHERS(f32)
+PQMC_DECLARE_LAUNCHERS(f32_256)
+PQMC_DECLARE_LAUNCHERS(f32_512)
 PQMC_DECLARE_LAUNCHERS(f32_dense)
 
 }  // namespace pqmc
