@@ -131,6 +131,13 @@ def test_empty_batch_rejected(lib):
     assert e.value.status == pqmc.EINVAL
 
 
+def test_null_context_queries_return_zero(lib):
+    """The size and count queries accept a NULL context (no device work)."""
+    assert lib.pqmc_device_bytes(None) == 0
+    assert lib.pqmc_upload_bytes(None) == 0
+    assert lib.pqmc_num_chains(None) == -1
+
+
 def test_autotune_cache_file_is_read(tmp_path):
     """The autotuner's JSON cache (PQMC_AUTOTUNE_CACHE): a stored pick for the
     batch's key is returned without timing anything (so no GPU is needed)."""
